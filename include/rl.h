@@ -1,0 +1,181 @@
+/*
+ * rl.h -- C ABI of the GB300 (sm_103a) batched multi-robot environment step.
+ *
+ * The method: JaxRobotarium (arXiv 2505.06771).  Each step of each environment
+ *   - forms the projected points p_i = (x_i + l cos th_i, y_i + l sin th_i) that the
+ *     single-integrator (SI) layer drives (Sec. 4.1: "single integrator and unicycle
+ *     controllers");
+ *   - takes a nominal SI velocity per robot: the policy's action, or the scripted go-to-target
+ *     law (Sec. 6.1 ControllerManager: waypoint -> controller) with uniform action noise
+ *     (Sec. 7, domain randomisation), capped to v_max;
+ *   - filters it through the barrier-certificate QP (Sec. 4.1: "control barrier certificates
+ *     ... solve the quadratic program"), min |u - u_nom|^2 subject to
+ *     -2 (p_i - p_j).(u_i - u_j) <= gamma h_ij^3, h_ij = |p_i - p_j|^2 - r^2, for every pair, and
+ *     four arena rows per robot, +-u_{x,y} <= kappa gamma (distance to the wall - r/2)^3;
+ *   - maps SI to unicycle velocities, clips the wheel speeds (Sec. 1: GRITSBot "dynamic
+ *     constraints"), integrates the unicycle model (Sec. 4.1) with explicit Euler;
+ *   - computes collision / boundary flags, the team reward, the scenario transition, done and
+ *     auto-reset, and the per-robot observations (App. B: Navigation, Foraging).
+ * The calls follow the Dec-POMDP reading of the Scenario interface (Sec. 6.1): per-agent
+ * observations, one shared team reward per environment, one done flag per environment.
+ *
+ * Conventions.
+ *   Ownership: every d_* pointer is device memory owned by the caller; host pointers are named
+ *   h_*.  Environment state lives in device memory owned by the handle.
+ *   Precision: a handle computes in binary32 (RL_PREC_F32) or binary64 (RL_PREC_F64); every
+ *   real-valued buffer of a call (actions, observations, rewards, traces) has that type.
+ *   Layout: the robots of env e occupy rows [off_e, off_e + n_e) of every per-robot buffer,
+ *   off_e = n_0 + ... + n_{e-1}; per-robot observations are rows of obs_dim values; per-env
+ *   buffers have one entry per env.  Trajectories are [T][rows...] with step t outermost.
+ *   Streams: calls are enqueued on the handle's stream and return before the GPU finishes.
+ *   Errors: argument errors are returned at once; CUDA errors are returned by the call that
+ *   sees them; rl_last_error() holds a one-line message.  Nothing aborts and no C++ exception
+ *   crosses this boundary.
+ */
+#ifndef ROBO_GB300_RL_H
+#define ROBO_GB300_RL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rl_env rl_env;
+
+typedef enum {
+    RL_OK = 0,
+    RL_ERR_ARG = 1,      /* invalid argument (size, pointer, configuration) */
+    RL_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    RL_ERR_OOM = 3,      /* device allocation failed */
+    RL_ERR_STATE = 4,    /* call not valid in the handle's state */
+    RL_ERR_TIMEOUT = 5,  /* a bounded device wait ran out */
+    RL_ERR_BUDGET = 6    /* a request can never fit the memory budget */
+} rl_status;
+
+typedef enum { RL_SCEN_NAVIGATION = 0, RL_SCEN_FORAGING = 1 } rl_scenario;
+typedef enum { RL_PREC_F32 = 32, RL_PREC_F64 = 64 } rl_precision;
+
+/* Counters per env (int32, cumulative since rl_create / rl_reset). */
+enum {
+    RL_CNT_COLLISIONS = 0,   /* colliding pairs summed over steps: |p_i - p_j|^2 < r^2 */
+    RL_CNT_OOB = 1,          /* robots whose projected point left the arena, summed over steps */
+    RL_CNT_SUCCESS = 2,      /* foraged resources */
+    RL_CNT_QP_ACTIVE = 3,    /* steps whose QP had at least one active row */
+    RL_CNT_QP_FLAGGED = 4,   /* steps whose binary32 QP was flagged and re-solved in binary64 */
+    RL_CNT_QP_INFEASIBLE = 5,/* steps whose QP was infeasible (the env's robots then stop) */
+    RL_CNT_EPISODES = 6,     /* completed episodes */
+    RL_CNT_QP_ITERS = 7,     /* active-set iterations summed over steps */
+    RL_NCOUNT = 8
+};
+
+/* Configuration.  rl_config_default() fills the constants of the paper's setting. */
+typedef struct {
+    int32_t scenario;       /* rl_scenario */
+    int32_t precision;      /* rl_precision */
+    int32_t scripted;       /* 1: scripted nominal control; 0: rl_step takes policy actions */
+    int32_t episode_len;    /* steps per episode (App. B: 100) */
+    int32_t n_res_min;      /* foraging: resources per episode, uniform in [min, max] */
+    int32_t n_res_max;
+    int32_t r_max;          /* foraging: resource slots in the observation (>= n_res_max) */
+    int32_t n_max;          /* robot slots in the observation (0: the largest n_e) */
+    int32_t max_attempts;   /* rejection-sampling attempts per robot at reset */
+    int32_t qp_max_iter;    /* active-set iteration cap (0: 8 * n_max + 16) */
+    int32_t resolve_f64;    /* 1: re-solve flagged binary32 QPs in binary64 */
+    int32_t lanes;          /* lanes per environment (0: chosen by the library's tuner) */
+    double gamma;           /* barrier gain (100) */
+    double r;               /* safety radius [m] (0.17) */
+    double l;               /* projection distance [m] (0.05) */
+    double vmax;            /* speed cap and wheel-speed limit [m/s] (0.2) */
+    double wmax;            /* turn-rate limit [rad/s] (3.6) */
+    double dt;              /* step [s] (0.033) */
+    double kappa;           /* arena-row gain factor (0.4) */
+    double k_si;            /* SI go-to-target gain (1.0) */
+    double noise_amp;       /* action noise U(-a, a) per component (0.05) */
+    double c_col;           /* collision penalty (1 Navigation, 0 Foraging) */
+    double forage_radius;   /* [m] (0.25) */
+    double xmin, xmax, ymin, ymax;   /* arena [m] (3.2 x 2.0 centred) */
+    double init_margin;     /* reset: distance of sampled points from the walls [m] (0.2) */
+    double min_sep;         /* reset: pairwise separation of robot centres [m] (0.3) */
+    double near_frac;       /* reset: share of envs with one near pair (0) */
+    double near_dmin, near_dmax;     /* reset: distance of the near pair [m] (0.18, 0.20) */
+    double h_flag;          /* flag a binary32 QP with an active pair whose h < h_flag (1e-3) */
+} rl_config;
+
+/* Optional outputs of one step (any pointer may be NULL). */
+typedef struct {
+    const void* d_actions;  /* [rows][2] policy SI velocities; NULL in scripted mode */
+    void* d_obs;            /* [rows][obs_dim] observations after the step (after auto-reset) */
+    void* d_reward;         /* [E] team reward of the transition */
+    uint8_t* d_done;        /* [E] 1 if the episode ended (the env was reset) */
+    void* d_u_nom;          /* [rows][2] nominal SI velocity after the speed cap */
+    void* d_u_star;         /* [rows][2] QP minimiser (filtered SI velocity) */
+    void* d_vw;             /* [rows][2] unicycle (v, omega) after the wheel clip */
+    int32_t* d_qp_info;     /* [E][4] status (0 ok, 1 infeasible, 2 iteration cap), active rows,
+                               iterations, flags (bit0 any active row, bit1 re-solved in FP64) */
+} rl_step_io;
+
+/* Fill *out with the defaults of a scenario.  RL_ERR_ARG on an unknown scenario. */
+rl_status rl_config_default(int32_t scenario, rl_config* out);
+
+/* Create a batch of n_envs environments and reset them (episode 0) with seed.
+   h_n_robots: host array [n_envs] of robot counts in [1, 32], or NULL to give every env
+   n_robots_uniform robots.  stream: a cudaStream_t; NULL makes the handle create its own
+   stream, which is ordered with the legacy default stream.
+   The handle allocates and owns the device state.  RL_ERR_ARG on bad sizes or configuration,
+   RL_ERR_OOM when the state does not fit. */
+rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_robots,
+                    int32_t n_robots_uniform, uint64_t seed, void* stream, rl_env** out);
+
+/* Reset every env to episode 0 under a new seed and zero the counters. */
+rl_status rl_reset(rl_env* env, uint64_t seed);
+
+/* One step of every env (Dec-POMDP step: joint action -> per-agent observations, team reward,
+   done).  d_actions is required unless the handle is scripted; the others may be NULL. */
+rl_status rl_step(rl_env* env, const void* d_actions, void* d_obs, void* d_reward,
+                  uint8_t* d_done);
+
+/* rl_step with the optional traces of rl_step_io. */
+rl_status rl_step_io_call(rl_env* env, const rl_step_io* io);
+
+/* T scripted steps of every env in one persistent launch (replayed from a CUDA graph), the
+   state kept on chip across steps.  d_obs_traj [T][rows][obs_dim], d_rew_traj [T][E],
+   d_done_traj [T][E]; any may be NULL.  RL_ERR_STATE if the handle is not scripted. */
+rl_status rl_rollout(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew_traj,
+                     uint8_t* d_done_traj);
+
+/* The same T steps in the plain form: one kernel launch per env per step, state through
+   global memory.  Same results as rl_rollout; kept as the per-env baseline. */
+rl_status rl_rollout_plain(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew_traj,
+                           uint8_t* d_done_traj);
+
+/* End to end through host memory: upload h_state (rl_state_bytes() bytes, or NULL to keep the
+   device state), run rl_rollout, and copy the trajectories to the host buffers (pinned memory
+   recommended; any may be NULL).  Returns after the copies completed. */
+rl_status rl_rollout_host(rl_env* env, const void* h_state, int32_t T, void* h_obs_traj,
+                          void* h_rew_traj, uint8_t* h_done_traj);
+
+/* Checkpoint: the full state (poses, goals, levels, step and episode counters, resources,
+   counters) as a self-describing blob.  Copies complete before return. */
+size_t    rl_state_bytes(const rl_env* env);
+rl_status rl_get_state(rl_env* env, void* h_dst, size_t bytes);
+rl_status rl_set_state(rl_env* env, const void* h_src, size_t bytes);
+
+/* Counters [E][RL_NCOUNT] to host memory (synchronises the stream). */
+rl_status rl_get_counters(rl_env* env, int32_t* h_dst);
+
+/* Wait for the handle's stream; returns RL_ERR_CUDA if the device reported an error. */
+rl_status rl_sync(rl_env* env);
+
+int32_t     rl_obs_dim(const rl_env* env);
+int32_t     rl_n_envs(const rl_env* env);
+int32_t     rl_total_robots(const rl_env* env);
+int32_t     rl_lanes(const rl_env* env);        /* lanes per env the handle runs with */
+const char* rl_last_error(const rl_env* env);   /* never NULL */
+void        rl_destroy(rl_env* env);            /* NULL-safe; waits for the stream */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

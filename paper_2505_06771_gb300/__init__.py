@@ -1,0 +1,294 @@
+"""Python binding of the GB300 batched multi-robot environment step (include/rl.h).
+
+The environment is JaxRobotarium's (arXiv 2505.06771): GRITSBot unicycles driven through a
+single-integrator controller and a barrier-certificate QP safety filter (Sec. 4.1), the
+ControllerManager ordering (Sec. 6.1), Navigation and Foraging scenarios (App. B).  Every step
+runs in the CUDA library ``_build/librobo_gb300.so``; this module only marshals arguments
+(torch tensors -> device pointers, the torch stream -> a cudaStream_t).  There is no CPU path:
+if the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from .build import LIB as LIB_PATH
+from .build import build
+
+__all__ = ["build", "lib", "config_default", "Env", "RLError", "NAVIGATION", "FORAGING",
+           "COUNTERS", "exported_symbols"]
+
+NAVIGATION, FORAGING = 0, 1
+COUNTERS = ("collisions", "oob", "success", "qp_active", "qp_flagged", "qp_infeasible",
+            "episodes", "qp_iters")
+_STATUS = {0: "RL_OK", 1: "RL_ERR_ARG", 2: "RL_ERR_CUDA", 3: "RL_ERR_OOM", 4: "RL_ERR_STATE",
+           5: "RL_ERR_TIMEOUT", 6: "RL_ERR_BUDGET"}
+_HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                    "rl.h")
+
+
+class RLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RLConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("scenario", "precision", "scripted", "episode_len", "n_res_min", "n_res_max",
+                 "r_max", "n_max", "max_attempts", "qp_max_iter", "resolve_f64", "lanes")] + \
+               [(n, ctypes.c_double) for n in
+                ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
+                 "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
+                 "near_frac", "near_dmin", "near_dmax", "h_flag")]
+
+
+class RLStepIO(ctypes.Structure):
+    _fields_ = [("d_actions", ctypes.c_void_p), ("d_obs", ctypes.c_void_p),
+                ("d_reward", ctypes.c_void_p), ("d_done", ctypes.c_void_p),
+                ("d_u_nom", ctypes.c_void_p), ("d_u_star", ctypes.c_void_p),
+                ("d_vw", ctypes.c_void_p), ("d_qp_info", ctypes.c_void_p)]
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def exported_symbols() -> list[str]:
+    """Function names declared in include/rl.h."""
+    src = open(_HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rl_[a-z_0-9]+)\s*\(", src)))
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing ({LIB_PATH}); run "
+                               "paper_2505_06771_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+        L.rl_config_default.argtypes = [i32, ctypes.POINTER(RLConfig)]
+        L.rl_create.argtypes = [ctypes.POINTER(RLConfig), i32, vp, i32, u64, vp,
+                                ctypes.POINTER(vp)]
+        L.rl_reset.argtypes = [vp, u64]
+        L.rl_step.argtypes = [vp, vp, vp, vp, vp]
+        L.rl_step_io_call.argtypes = [vp, ctypes.POINTER(RLStepIO)]
+        L.rl_rollout.argtypes = [vp, i32, vp, vp, vp]
+        L.rl_rollout_plain.argtypes = [vp, i32, vp, vp, vp]
+        L.rl_rollout_host.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.rl_state_bytes.argtypes = [vp]
+        L.rl_state_bytes.restype = sz
+        L.rl_get_state.argtypes = [vp, vp, sz]
+        L.rl_set_state.argtypes = [vp, vp, sz]
+        L.rl_get_counters.argtypes = [vp, vp]
+        L.rl_sync.argtypes = [vp]
+        for f in ("rl_obs_dim", "rl_n_envs", "rl_total_robots", "rl_lanes"):
+            getattr(L, f).argtypes = [vp]
+            getattr(L, f).restype = i32
+        L.rl_last_error.argtypes = [vp]
+        L.rl_last_error.restype = ctypes.c_char_p
+        L.rl_destroy.argtypes = [vp]
+        L.rl_destroy.restype = None
+        _LIB = L
+        return L
+
+
+def config_default(scenario: int = NAVIGATION, **overrides) -> dict:
+    c = RLConfig()
+    st = lib().rl_config_default(scenario, ctypes.byref(c))
+    if st:
+        raise RLError(st, "rl_config_default")
+    d = {name: getattr(c, name) for name, _ in RLConfig._fields_}
+    for k in overrides:
+        if k not in d:
+            raise KeyError(k)
+    d.update(overrides)
+    return d
+
+
+def _to_struct(cfg: dict) -> RLConfig:
+    c = RLConfig()
+    for name, _ in RLConfig._fields_:
+        setattr(c, name, cfg[name])
+    return c
+
+
+def _dptr(t, dtype, numel=None, name="buffer"):
+    """Device pointer of a contiguous CUDA tensor of the expected dtype (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: needs {numel} elements, has {t.numel()}")
+    return t.data_ptr()
+
+
+def _hptr(a, numel, itemsize, name):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.nbytes < numel * itemsize:
+            raise ValueError(f"{name}: contiguous host array of {numel} items needed")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda and a.is_contiguous():
+        if a.numel() * a.element_size() < numel * itemsize:
+            raise ValueError(f"{name}: too small")
+        return a.data_ptr()
+    raise TypeError(f"{name}: expected a contiguous host array")
+
+
+class Env:
+    """A batch of environments on the current CUDA device (one rl_env handle)."""
+
+    def __init__(self, cfg: dict, n_envs: int, n_robots, seed: int = 0, stream=None):
+        import torch
+        L = lib()
+        self._L = L
+        self.cfg = dict(cfg)
+        if isinstance(n_robots, (int, np.integer)):
+            arr, uni = None, int(n_robots)
+            self.n_robots = np.full(n_envs, uni, np.int32)
+        else:
+            arr = np.ascontiguousarray(n_robots, dtype=np.int32)
+            if len(arr) != n_envs:
+                raise ValueError("n_robots must have n_envs entries")
+            uni = 0
+            self.n_robots = arr
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = L.rl_create(ctypes.byref(_to_struct(self.cfg)), n_envs,
+                         None if arr is None else arr.ctypes.data, uni, seed,
+                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st:
+            raise RLError(st, "rl_create")
+        self._h = h
+        self.n_envs = n_envs
+        self.obs_dim = int(L.rl_obs_dim(h))
+        self.total_robots = int(L.rl_total_robots(h))
+        self.lanes = int(L.rl_lanes(h))
+        self.dtype = torch.float64 if self.cfg["precision"] == 64 else torch.float32
+        self.np_dtype = np.float64 if self.cfg["precision"] == 64 else np.float32
+        self.off = np.concatenate([[0], np.cumsum(self.n_robots)]).astype(np.int64)
+
+    # ------------------------------------------------------------------ calls
+    def _check(self, st, what):
+        if st:
+            raise RLError(st, f"{what}: {self._L.rl_last_error(self._h).decode()}")
+
+    def reset(self, seed: int):
+        self._check(self._L.rl_reset(self._h, seed), "rl_reset")
+
+    def step(self, actions=None, obs=None, reward=None, done=None, u_nom=None, u_star=None,
+             vw=None, qp_info=None):
+        import torch
+        R, E = self.total_robots, self.n_envs
+        io = RLStepIO(_dptr(actions, self.dtype, 2 * R, "actions"),
+                      _dptr(obs, self.dtype, R * self.obs_dim, "obs"),
+                      _dptr(reward, self.dtype, E, "reward"),
+                      _dptr(done, torch.uint8, E, "done"),
+                      _dptr(u_nom, self.dtype, 2 * R, "u_nom"),
+                      _dptr(u_star, self.dtype, 2 * R, "u_star"),
+                      _dptr(vw, self.dtype, 2 * R, "vw"),
+                      _dptr(qp_info, torch.int32, 4 * E, "qp_info"))
+        self._check(self._L.rl_step_io_call(self._h, ctypes.byref(io)), "rl_step")
+
+    def rollout(self, T: int, obs=None, reward=None, done=None, plain: bool = False):
+        import torch
+        R, E = self.total_robots, self.n_envs
+        f = self._L.rl_rollout_plain if plain else self._L.rl_rollout
+        self._check(f(self._h, T, _dptr(obs, self.dtype, T * R * self.obs_dim, "obs"),
+                      _dptr(reward, self.dtype, T * E, "reward"),
+                      _dptr(done, torch.uint8, T * E, "done")), "rl_rollout")
+
+    def rollout_host(self, T: int, state=None, obs=None, reward=None, done=None):
+        R, E = self.total_robots, self.n_envs
+        isz = 8 if self.cfg["precision"] == 64 else 4
+        sp = None
+        if state is not None:
+            sb = np.frombuffer(state, np.uint8) if isinstance(state, (bytes, bytearray)) else state
+            sp = _hptr(sb, self.state_bytes(), 1, "state")
+        self._check(self._L.rl_rollout_host(self._h, sp, T,
+                                            _hptr(obs, T * R * self.obs_dim, isz, "obs"),
+                                            _hptr(reward, T * E, isz, "reward"),
+                                            _hptr(done, T * E, 1, "done")), "rl_rollout_host")
+
+    def state_bytes(self) -> int:
+        return int(self._L.rl_state_bytes(self._h))
+
+    def get_state(self) -> bytes:
+        n = self.state_bytes()
+        buf = ctypes.create_string_buffer(n)
+        self._check(self._L.rl_get_state(self._h, buf, n), "rl_get_state")
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        self._check(self._L.rl_set_state(self._h, blob, len(blob)), "rl_set_state")
+
+    def counters(self) -> np.ndarray:
+        out = np.zeros((self.n_envs, 8), np.int32)
+        self._check(self._L.rl_get_counters(self._h, out.ctypes.data), "rl_get_counters")
+        return out
+
+    def sync(self):
+        self._check(self._L.rl_sync(self._h), "rl_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ state blob
+    def state_arrays(self, blob: bytes | None = None) -> dict:
+        """Parse a state blob (header + image of 256-byte-aligned segments) into arrays."""
+        return parse_state(blob if blob is not None else self.get_state())
+
+
+_SEGS = [("x", "r", "T"), ("y", "r", "T"), ("th", "r", "T"), ("gx", "r", "T"), ("gy", "r", "T"),
+         ("level", "i", "T"), ("t", "i", "E"), ("ep", "i", "E"), ("n_res", "i", "E"),
+         ("qx", "r", "RM"), ("qy", "r", "RM"), ("qlevel", "i", "RM"), ("qactive", "i", "RM"),
+         ("counters", "i", "C"), ("n_robots", "i", "E"), ("off", "i", "E1")]
+
+
+def parse_state(blob: bytes) -> dict:
+    hdr = np.frombuffer(blob, np.int32, 10)
+    magic, version, prec, scen, E, T, rmax, nmax = [int(v) for v in hdr[:8]]
+    if magic != 0x31534C52 or version != 1:
+        raise ValueError("not a state blob")
+    seed, img = np.frombuffer(blob, np.uint64, 2, offset=32)
+    rdt = np.float64 if prec == 64 else np.float32
+    counts = dict(T=T, E=E, RM=E * rmax, C=E * 8, E1=E + 1)
+    out = dict(precision=prec, scenario=scen, n_envs=E, total_robots=T, r_max=rmax, n_max=nmax,
+               seed=int(seed))
+    pos = 64
+    for name, kind, cnt in _SEGS:
+        dt = rdt if kind == "r" else np.int32
+        n = counts[cnt]
+        nbytes = n * np.dtype(dt).itemsize
+        out[name] = np.frombuffer(blob, dt, n, offset=pos).copy()
+        pos += (nbytes + 255) & ~255
+    out["counters"] = out["counters"].reshape(E, 8)
+    return out

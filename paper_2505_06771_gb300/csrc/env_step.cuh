@@ -1,0 +1,1175 @@
+// env_step.cuh -- device code of the batched multi-robot environment step (sm_103a).
+//
+// One environment is handled by a *team* of G consecutive lanes of a warp (G in 1..32, a power
+// of two).  Robot i of the env is owned by lane i mod G, which keeps its pose, goal and cached
+// heading sine/cosine in registers for the whole launch (a rollout of T steps never round-trips
+// the state through global memory).  What lanes need from each other -- projected points, the
+// QP iterate, the active set and its Cholesky factor -- sits in a per-team slice of shared
+// memory; team-wide reductions use warp shuffles over width G.
+//
+// The step (JaxRobotarium, arXiv 2505.06771, Sec. 4.1 and 6.1, App. B):
+//   projected points -> nominal SI velocity (policy action, or go-to-target + noise) -> speed cap
+//   -> barrier-certificate QP -> SI-to-unicycle map -> wheel clip -> Euler step -> flags, reward,
+//   scenario transition -> done and auto-reset -> observations.
+//
+// The QP, min |u - u_nom|^2 s.t. A u <= b, is a Euclidean projection (Hessian 2I), solved by the
+// dual active-set method of Goldfarb and Idnani (1983): start at u_nom, add the most violated row,
+// step along z = (I - N G^-1 N^T) a_p in the primal and r = G^-1 N^T a_p in the dual, drop rows
+// whose multiplier would go negative.  G = N^T N (Gram of the active rows, at most 2N of them) is
+// kept as a Cholesky factor that grows by one row per added constraint.  Row j's violation is
+// evaluated on the fly from the projected points, so the m = N(N-1)/2 + 4N rows are never stored.
+// Pair rows are spread over the lanes by a circulant schedule (robot i owns pairs (i, i+d mod N),
+// d = 1..floor((N-1)/2), plus d = N/2 for i < N/2 when N is even), which balances them with no
+// index table.  In binary32 a QP that hits the iteration cap, meets a nearly dependent row, is
+// infeasible, or keeps an active pair with h < h_flag is re-solved in binary64 by the same team.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <type_traits>
+
+#include "philox.cuh"
+
+namespace rl {
+
+constexpr int kMaxRobots = 32;
+constexpr int kMaxRes = 16;
+constexpr int kNCount = 8;
+
+template <typename R>
+struct StepConsts {
+    R gamma, r2, l, inv_l, vmax, half_track, inv_track, dt, kg, half_r, k_si, c_col, rho2;
+    R xmin, xmax, ymin, ymax, h_flag;
+    int scenario, scripted, episode_len, max_iter, n_res_min, n_res_max, r_max, n_max_obs;
+    int max_attempts, resolve_f64, noise_on;
+    float noise_scale;  // 2 * noise amplitude, binary32 (the noise draw is binary32)
+};
+
+// Reset-sampler constants, binary32, computed on the host with one rounding each.
+struct SamplerConsts {
+    float lox, hix, loy, hiy, wx, wy, sep2, pif, twopif, near_frac, dmin, dspan;
+    int near_on;
+};
+
+template <typename R>
+struct StateView {
+    R *x, *y, *th, *gx, *gy;
+    int32_t* level;
+    int32_t *t, *ep, *n_res;
+    R *qx, *qy;
+    int32_t *qlevel, *qactive;
+    int32_t* counters;
+    const int32_t* off;   // [E + 1] first row of each env
+    const int32_t* nrob;  // [E]
+};
+
+template <typename R>
+struct StepIO {
+    const R* actions;  // [rows][2] (T == 1 only)
+    R* obs;            // [T][rows][obs_dim]
+    R* reward;         // [T][E]
+    uint8_t* done;     // [T][E]
+    R* u_nom;          // [rows][2] traces (T == 1 only)
+    R* u_star;
+    R* vw;
+    int32_t* qp_info;  // [E][4]
+    long long obs_step;  // rows * obs_dim
+    int E;
+    int obs_dim;
+};
+
+template <typename R>
+struct LaunchArgs {
+    StateView<R> s;
+    StepIO<R> io;
+    StepConsts<R> k;
+    SamplerConsts sc;
+    const int32_t* env_list;  // env ids of this launch (NULL: env_begin + index)
+    int n_list;
+    int env_begin;
+    int T;
+    uint64_t seed;
+};
+
+// ------------------------------------------------------------------------------------------
+// Team of G lanes
+// ------------------------------------------------------------------------------------------
+template <int G>
+struct Team {
+    static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "team size must be a power of two");
+    int lane;
+    int base;
+    unsigned mask;
+    __device__ __forceinline__ Team() {
+        const int wl = threadIdx.x & 31;
+        lane = wl & (G - 1);
+        base = wl & ~(G - 1);
+        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    template <typename T>
+    __device__ __forceinline__ T sum(T v) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+        return v;
+    }
+    __device__ __forceinline__ unsigned ballot(bool p) const {
+        const unsigned b = __ballot_sync(mask, p);
+        return (G == 32) ? b : ((b >> base) & ((1u << G) - 1u));
+    }
+    __device__ __forceinline__ bool any(bool p) const { return ballot(p) != 0u; }
+    // max of v, ties to the smallest key (all lanes get the result)
+    template <typename T>
+    __device__ __forceinline__ void argmax(T& v, int& key) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(mask, v, o, G);
+            const int ok = __shfl_xor_sync(mask, key, o, G);
+            if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
+        }
+    }
+    template <typename T>
+    __device__ __forceinline__ void argmin(T& v, int& key) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(mask, v, o, G);
+            const int ok = __shfl_xor_sync(mask, key, o, G);
+            if (ov < v || (ov == v && ok < key)) { v = ov; key = ok; }
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// Shared-memory workspace of one team
+// ------------------------------------------------------------------------------------------
+template <typename Q, int NMAX>
+struct QPWork {
+    static constexpr int A = 2 * NMAX;                          // active rows at most
+    static constexpr int M = NMAX * (NMAX - 1) / 2 + 4 * NMAX;  // rows
+    Q px[NMAX], py[NMAX];
+    Q ux[NMAX], uy[NMAX];
+    Q u0x[NMAX], u0y[NMAX];
+    Q lam[A], w[A], yv[A], rv[A], rb[A], rax[A], ray[A];
+    Q L[A * A];
+    int ria[A], rib[A], rk[A];
+    unsigned actbits[(M + 31) / 32];
+    int fail;
+};
+
+template <int NMAX>
+union QPUnion {
+    QPWork<float, NMAX> f;
+    QPWork<double, NMAX> d;
+};
+
+template <typename R, int NMAX>
+struct TeamSmem {
+    QPUnion<NMAX> qp;
+    R sx[NMAX], sy[NMAX], sth[NMAX];
+    int slevel[NMAX];
+    R qx[kMaxRes], qy[kMaxRes];
+    int qlevel[kMaxRes], qactive[kMaxRes];
+    float fx[NMAX], fy[NMAX], fth[NMAX];
+};
+
+template <typename Q, int NMAX>
+struct WorkSel;
+template <int NMAX>
+struct WorkSel<float, NMAX> {
+    static __device__ __forceinline__ QPWork<float, NMAX>& get(QPUnion<NMAX>& u) { return u.f; }
+};
+template <int NMAX>
+struct WorkSel<double, NMAX> {
+    static __device__ __forceinline__ QPWork<double, NMAX>& get(QPUnion<NMAX>& u) { return u.d; }
+};
+
+template <typename Q>
+struct QPConsts {
+    Q gamma, r2, kg, half_r, xmin, xmax, ymin, ymax, tol_abs, tol_rel, eps_dep, tol_lam, h_flag;
+    int max_iter;
+};
+
+struct QPResult {
+    int status;  // 0 ok, 1 infeasible, 2 iteration cap or numerical failure
+    int q;       // active rows
+    int iters;
+    bool flag;   // needs the binary64 re-solve (binary32 only)
+};
+
+template <typename Q>
+__device__ __forceinline__ Q qinf() { return (Q)CUDART_INF; }
+template <>
+__device__ __forceinline__ float qinf<float>() { return CUDART_INF_F; }
+
+__device__ __forceinline__ float qsqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double qsqrt(double v) { return sqrt(v); }
+
+// Coefficients of one QP row: (ax, ay) on u_ia and, for a pair row, (-ax, -ay) on u_ib.
+template <typename Q>
+__device__ __forceinline__ Q row_dot(int ia1, int ib1, Q ax1, Q ay1, int ia2, int ib2, Q ax2,
+                                     Q ay2) {
+    const Q cc = ax1 * ax2 + ay1 * ay2;
+    Q d = (Q)0;
+    if (ia1 == ia2) d += cc;
+    if (ib1 >= 0 && ib1 == ia2) d -= cc;
+    if (ib2 >= 0 && ia1 == ib2) d -= cc;
+    if (ib1 >= 0 && ib1 == ib2) d += cc;
+    return d;
+}
+
+__device__ __forceinline__ int pair_index(int a, int b, int N) {
+    return a * N - (a * (a + 1)) / 2 + (b - a - 1);
+}
+
+// Pair (a, b), a < b, of the lexicographic index k < N(N-1)/2.
+__device__ __forceinline__ void pair_of(int k, int N, int& a, int& b) {
+    int rem = k, i = 0;
+    while (rem >= N - 1 - i) {
+        rem -= N - 1 - i;
+        ++i;
+    }
+    a = i;
+    b = i + 1 + rem;
+}
+
+template <typename Q>
+struct RowInfo {
+    int k, ia, ib;
+    Q ax, ay, b;
+};
+
+template <typename Q, int NMAX>
+__device__ __forceinline__ RowInfo<Q> decode_row(const QPWork<Q, NMAX>& W, int k, int N,
+                                                 const QPConsts<Q>& c) {
+    RowInfo<Q> r;
+    r.k = k;
+    const int P = N * (N - 1) / 2;
+    if (k < P) {
+        int a, b;
+        pair_of(k, N, a, b);
+        const Q dx = W.px[a] - W.px[b], dy = W.py[a] - W.py[b];
+        const Q h = dx * dx + dy * dy - c.r2;
+        r.ia = a;
+        r.ib = b;
+        r.ax = (Q)-2 * dx;
+        r.ay = (Q)-2 * dy;
+        r.b = c.gamma * h * h * h;
+    } else {
+        const int i = (k - P) >> 2, s = (k - P) & 3;
+        r.ia = i;
+        r.ib = -1;
+        Q d;
+        if (s == 0) { r.ax = (Q)1; r.ay = (Q)0; d = c.xmax - c.half_r - W.px[i]; }
+        else if (s == 1) { r.ax = (Q)-1; r.ay = (Q)0; d = W.px[i] - c.xmin - c.half_r; }
+        else if (s == 2) { r.ax = (Q)0; r.ay = (Q)1; d = c.ymax - c.half_r - W.py[i]; }
+        else { r.ax = (Q)0; r.ay = (Q)-1; d = W.py[i] - c.ymin - c.half_r; }
+        r.b = c.kg * d * d * d;
+    }
+    return r;
+}
+
+// Most violated inactive row (violation beyond tolerance); key INT_MAX if none.
+template <typename Q, int G, int NMAX>
+__device__ __forceinline__ void scan_rows(const Team<G>& tm, const QPWork<Q, NMAX>& W, int N,
+                                          const QPConsts<Q>& c, Q& vbest, int& kbest) {
+    constexpr int RPL = (NMAX + G - 1) / G;
+    const int P = N * (N - 1) / 2;
+    vbest = (Q)0;
+    kbest = 0x7fffffff;
+    const int nd = (N - 1) / 2;
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+        const int i = tm.lane + s * G;
+        if (i < N) {
+            const int ndi = nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0);
+            for (int d = 1; d <= ndi; ++d) {
+                int j = i + d;
+                if (j >= N) j -= N;
+                const int a = min(i, j), b = max(i, j);
+                const int k = pair_index(a, b, N);
+                if ((W.actbits[k >> 5] >> (k & 31)) & 1u) continue;
+                const Q dx = W.px[a] - W.px[b], dy = W.py[a] - W.py[b];
+                const Q h = dx * dx + dy * dy - c.r2;
+                const Q bv = c.gamma * h * h * h;
+                const Q au = (Q)-2 * (dx * (W.ux[a] - W.ux[b]) + dy * (W.uy[a] - W.uy[b]));
+                const Q v = au - bv;
+                if (v > c.tol_abs + c.tol_rel * fabs(bv) && (v > vbest || (v == vbest && k < kbest))) {
+                    vbest = v;
+                    kbest = k;
+                }
+            }
+            const Q bx0 = c.xmax - c.half_r - W.px[i], bx1 = W.px[i] - c.xmin - c.half_r;
+            const Q by0 = c.ymax - c.half_r - W.py[i], by1 = W.py[i] - c.ymin - c.half_r;
+            const Q bvs[4] = {c.kg * bx0 * bx0 * bx0, c.kg * bx1 * bx1 * bx1,
+                              c.kg * by0 * by0 * by0, c.kg * by1 * by1 * by1};
+            const Q aus[4] = {W.ux[i], -W.ux[i], W.uy[i], -W.uy[i]};
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                const int k = P + 4 * i + q4;
+                if ((W.actbits[k >> 5] >> (k & 31)) & 1u) continue;
+                const Q v = aus[q4] - bvs[q4];
+                if (v > c.tol_abs + c.tol_rel * fabs(bvs[q4]) &&
+                    (v > vbest || (v == vbest && k < kbest))) {
+                    vbest = v;
+                    kbest = k;
+                }
+            }
+        }
+    }
+    tm.argmax(vbest, kbest);
+}
+
+// Cholesky factor of the Gram matrix of the active rows, from scratch (leader lane only).
+template <typename Q, int NMAX>
+__device__ bool refactor(QPWork<Q, NMAX>& W, int q) {
+    constexpr int A = QPWork<Q, NMAX>::A;
+    for (int i = 0; i < q; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            Q s = row_dot(W.ria[i], W.rib[i], W.rax[i], W.ray[i], W.ria[j], W.rib[j], W.rax[j],
+                          W.ray[j]);
+            for (int k = 0; k < j; ++k) s -= W.L[i * A + k] * W.L[j * A + k];
+            if (i == j) {
+                if (!(s > (Q)0)) return false;
+                W.L[i * A + i] = qsqrt(s);
+            } else {
+                W.L[i * A + j] = s / W.L[j * A + j];
+            }
+        }
+    }
+    return true;
+}
+
+// L y = w, then L^T r = y (leader lane only).
+template <typename Q, int NMAX>
+__device__ __forceinline__ void chol_solve(QPWork<Q, NMAX>& W, int q, const Q* rhs, Q* y, Q* r) {
+    constexpr int A = QPWork<Q, NMAX>::A;
+    for (int i = 0; i < q; ++i) {
+        Q s = rhs[i];
+        for (int k = 0; k < i; ++k) s -= W.L[i * A + k] * y[k];
+        y[i] = s / W.L[i * A + i];
+    }
+    for (int i = q - 1; i >= 0; --i) {
+        Q s = y[i];
+        for (int k = i + 1; k < q; ++k) s -= W.L[k * A + i] * r[k];
+        r[i] = s / W.L[i * A + i];
+    }
+}
+
+// Solve the team's QP.  On entry W.px/py, W.u0x/u0y and W.ux/uy (= u0) hold all N robots and
+// the team is synchronised; on exit W.ux/uy hold the minimiser (zero if infeasible), synced.
+template <typename Q, int G, int NMAX>
+__device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const QPConsts<Q>& c) {
+    constexpr int RPL = (NMAX + G - 1) / G;
+    constexpr int A = QPWork<Q, NMAX>::A;
+    const int P = N * (N - 1) / 2;
+    const int M = P + 4 * N;
+    for (int wd = tm.lane; wd < (M + 31) / 32; wd += G) W.actbits[wd] = 0u;
+    if (tm.lane == 0) W.fail = 0;
+    tm.sync();
+
+    QPResult res;
+    res.status = 0;
+    res.q = 0;
+    res.iters = 0;
+    res.flag = false;
+    int q = 0;
+    const Q INF = qinf<Q>();
+
+    for (;;) {
+        Q vbest;
+        int kbest;
+        scan_rows<Q, G, NMAX>(tm, W, N, c, vbest, kbest);
+        if (kbest == 0x7fffffff) break;
+        if (++res.iters > c.max_iter || q >= A) {
+            res.status = 2;
+            break;
+        }
+        const RowInfo<Q> p = decode_row<Q, NMAX>(W, kbest, N, c);
+        const Q app = (p.ib >= 0 ? (Q)2 : (Q)1) * (p.ax * p.ax + p.ay * p.ay);
+        Q lam_p = (Q)0;
+        bool added = false;
+        for (int guard = 0; guard <= A + 1 && !added; ++guard) {
+            for (int j = tm.lane; j < q; j += G)
+                W.w[j] = row_dot(W.ria[j], W.rib[j], W.rax[j], W.ray[j], p.ia, p.ib, p.ax, p.ay);
+            tm.sync();
+            if (tm.lane == 0) chol_solve<Q, NMAX>(W, q, W.w, W.yv, W.rv);
+            tm.sync();
+            // primal direction z on the lane's own robots
+            Q zx[RPL], zy[RPL];
+            Q zzl = (Q)0;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                Q ax = (Q)0, ay = (Q)0;
+                if (i < N) {
+                    if (p.ia == i) { ax += p.ax; ay += p.ay; }
+                    if (p.ib == i) { ax -= p.ax; ay -= p.ay; }
+                    for (int j = 0; j < q; ++j) {
+                        const Q rj = W.rv[j];
+                        if (W.ria[j] == i) { ax -= rj * W.rax[j]; ay -= rj * W.ray[j]; }
+                        if (W.rib[j] == i) { ax += rj * W.rax[j]; ay += rj * W.ray[j]; }
+                    }
+                }
+                zx[s] = ax;
+                zy[s] = ay;
+                zzl += ax * ax + ay * ay;
+            }
+            const Q zz = tm.sum(zzl);
+            // dual step bound
+            Q td = INF;
+            int jb = 0x7fffffff;
+            for (int j = tm.lane; j < q; j += G) {
+                const Q rj = W.rv[j];
+                if (rj > (Q)0) {
+                    const Q tj = W.lam[j] / rj;
+                    if (tj < td || (tj == td && j < jb)) { td = tj; jb = j; }
+                }
+            }
+            tm.argmin(td, jb);
+            // current violation of row p
+            Q ap_u;
+            if (p.ib >= 0)
+                ap_u = p.ax * (W.ux[p.ia] - W.ux[p.ib]) + p.ay * (W.uy[p.ia] - W.uy[p.ib]);
+            else
+                ap_u = p.ax * W.ux[p.ia] + p.ay * W.uy[p.ia];
+            const Q sp = ap_u - p.b;
+            const bool indep = zz > c.eps_dep * app;
+            if (!indep) res.flag = true;
+            const Q tf = indep ? sp / zz : INF;
+            if (!(tf < INF) && !(td < INF)) {
+                res.status = 1;
+                break;
+            }
+            const Q t = tf < td ? tf : td;
+            tm.sync();  // everyone has read W.ux / W.rv / W.lam
+            if (tf < INF) {
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        W.ux[i] -= t * zx[s];
+                        W.uy[i] -= t * zy[s];
+                    }
+                }
+            }
+            for (int j = tm.lane; j < q; j += G) W.lam[j] -= t * W.rv[j];
+            lam_p += t;
+            if (tf <= td) {
+                if (tm.lane == 0) {
+                    for (int jj = 0; jj < q; ++jj) W.L[q * A + jj] = W.yv[jj];
+                    W.L[q * A + q] = qsqrt(zz);
+                    W.ria[q] = p.ia;
+                    W.rib[q] = p.ib;
+                    W.rax[q] = p.ax;
+                    W.ray[q] = p.ay;
+                    W.rb[q] = p.b;
+                    W.rk[q] = p.k;
+                    W.lam[q] = lam_p;
+                    W.actbits[p.k >> 5] |= 1u << (p.k & 31);
+                }
+                ++q;
+                added = true;
+            } else {
+                tm.sync();
+                if (tm.lane == 0) {
+                    W.actbits[W.rk[jb] >> 5] &= ~(1u << (W.rk[jb] & 31));
+                    for (int j = jb; j < q - 1; ++j) {
+                        W.ria[j] = W.ria[j + 1];
+                        W.rib[j] = W.rib[j + 1];
+                        W.rax[j] = W.rax[j + 1];
+                        W.ray[j] = W.ray[j + 1];
+                        W.rb[j] = W.rb[j + 1];
+                        W.rk[j] = W.rk[j + 1];
+                        W.lam[j] = W.lam[j + 1];
+                    }
+                    if (!refactor<Q, NMAX>(W, q - 1)) W.fail = 1;
+                }
+                --q;
+            }
+            tm.sync();
+            if (W.fail) {
+                res.status = 2;
+                break;
+            }
+        }
+        if (res.status != 0) break;
+        if (!added) {
+            res.status = 2;
+            break;
+        }
+    }
+    res.q = q;
+
+    if (res.status == 0 && q > 0) {
+        // exact solve on the final active set: G lam = N^T u0 - b_A, u = u0 - N lam
+        for (int j = tm.lane; j < q; j += G) {
+            Q au0;
+            if (W.rib[j] >= 0)
+                au0 = W.rax[j] * (W.u0x[W.ria[j]] - W.u0x[W.rib[j]]) +
+                      W.ray[j] * (W.u0y[W.ria[j]] - W.u0y[W.rib[j]]);
+            else
+                au0 = W.rax[j] * W.u0x[W.ria[j]] + W.ray[j] * W.u0y[W.ria[j]];
+            W.w[j] = au0 - W.rb[j];
+        }
+        tm.sync();
+        if (tm.lane == 0) {
+            chol_solve<Q, NMAX>(W, q, W.w, W.yv, W.rv);
+            int bad = 0;
+            for (int j = 0; j < q; ++j)
+                if (W.rv[j] < -c.tol_lam) bad = 1;
+            W.fail = bad;
+        }
+        tm.sync();
+        const bool dual_ok = (W.fail == 0);
+        Q keepx[RPL], keepy[RPL];
+        if (dual_ok) {
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                keepx[s] = (Q)0;
+                keepy[s] = (Q)0;
+                if (i < N) {
+                    Q ux = W.u0x[i], uy = W.u0y[i];
+                    for (int j = 0; j < q; ++j) {
+                        const Q lj = W.rv[j];
+                        if (W.ria[j] == i) { ux -= lj * W.rax[j]; uy -= lj * W.ray[j]; }
+                        if (W.rib[j] == i) { ux += lj * W.rax[j]; uy += lj * W.ray[j]; }
+                    }
+                    keepx[s] = W.ux[i];
+                    keepy[s] = W.uy[i];
+                    W.ux[i] = ux;
+                    W.uy[i] = uy;
+                }
+            }
+            tm.sync();
+            // the polished point must stay feasible; otherwise keep the active-set iterate
+            for (int wd = tm.lane; wd < (M + 31) / 32; wd += G) W.actbits[wd] = 0u;
+            tm.sync();
+            Q vb;
+            int kb;
+            scan_rows<Q, G, NMAX>(tm, W, N, c, vb, kb);
+            tm.sync();
+            if (kb != 0x7fffffff) {
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        W.ux[i] = keepx[s];
+                        W.uy[i] = keepy[s];
+                    }
+                }
+            }
+        }
+        // binary32: an active pair with h below h_flag marks the QP near-degenerate
+        bool small_h = false;
+        for (int j = tm.lane; j < q; j += G) {
+            if (W.rib[j] >= 0) {
+                const Q dx = W.px[W.ria[j]] - W.px[W.rib[j]], dy = W.py[W.ria[j]] - W.py[W.rib[j]];
+                if (dx * dx + dy * dy - c.r2 < c.h_flag) small_h = true;
+            }
+        }
+        if (tm.any(small_h)) res.flag = true;
+    }
+    if (res.status == 1) {
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+            const int i = tm.lane + s * G;
+            if (i < N) {
+                W.ux[i] = (Q)0;
+                W.uy[i] = (Q)0;
+            }
+        }
+    }
+    if (res.status != 0) res.flag = true;
+    tm.sync();
+    return res;
+}
+
+// ------------------------------------------------------------------------------------------
+// Small helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void sc_(float v, float* s, float* c) { sincosf(v, s, c); }
+__device__ __forceinline__ void sc_(double v, double* s, double* c) { sincos(v, s, c); }
+
+template <typename R>
+__device__ __forceinline__ void cap_norm(R& ux, R& uy, R m) {
+    const R n2 = ux * ux + uy * uy;
+    if (n2 > m * m) {
+        const R s = m / qsqrt(n2);
+        ux *= s;
+        uy *= s;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R wrap_pi(R a) {
+    const R pi = (R)CUDART_PI, two_pi = (R)(2.0 * CUDART_PI);
+    if (a > pi) a -= two_pi;
+    else if (a <= -pi) a += two_pi;
+    return a;
+}
+
+template <typename R>
+__device__ __forceinline__ R hyp(R a, R b) { return qsqrt(a * a + b * b); }
+
+// ------------------------------------------------------------------------------------------
+// Reset sampler (binary32, every operation rounded on its own)
+// ------------------------------------------------------------------------------------------
+template <typename R, int G, int NMAX>
+__device__ void team_sample(const Team<G>& tm, TeamSmem<R, NMAX>& S, const LaunchArgs<R>& A,
+                            int e, int ep, int N, int& n_res) {
+    const SamplerConsts& sc = A.sc;
+    const uint64_t seed = A.seed;
+    const int max_att = A.k.max_attempts;
+    if (tm.lane == 0) {
+        const Words4 w = draw(seed, e, ep, kPos, 0, 0u);
+        S.fx[0] = __fadd_rn(sc.lox, __fmul_rn(unit24(w.w[0]), sc.wx));
+        S.fy[0] = __fadd_rn(sc.loy, __fmul_rn(unit24(w.w[1]), sc.wy));
+        S.fth[0] = __fadd_rn(-sc.pif, __fmul_rn(unit24(w.w[2]), sc.twopif));
+    }
+    tm.sync();
+    int first = 1;
+    if (N >= 2 && sc.near_on) {
+        const Words4 w = draw(seed, e, ep, kNear, 0, 0u);
+        if (unit24(w.w[0]) < sc.near_frac) {
+            for (int base = 0; base < max_att; base += G) {
+                const int a = base + tm.lane;
+                bool ok = false;
+                float x1 = 0.f, y1 = 0.f;
+                if (a < max_att) {
+                    const Words4 v = draw(seed, e, ep, kNear, 1, (uint32_t)a);
+                    const float d = __fadd_rn(sc.dmin, __fmul_rn(unit24(v.w[0]), sc.dspan));
+                    const float cx = __fsub_rn(__fmul_rn(2.0f, unit24(v.w[1])), 1.0f);
+                    const float cy = __fsub_rn(__fmul_rn(2.0f, unit24(v.w[2])), 1.0f);
+                    const float rr = __fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy));
+                    if (!(rr < 0.0625f || rr > 1.0f)) {
+                        const float nrm = __fsqrt_rn(rr);
+                        const float ox = __fdiv_rn(__fmul_rn(d, cx), nrm);
+                        const float oy = __fdiv_rn(__fmul_rn(d, cy), nrm);
+                        x1 = __fadd_rn(S.fx[0], ox);
+                        y1 = __fadd_rn(S.fy[0], oy);
+                        ok = !(x1 < sc.lox || x1 > sc.hix || y1 < sc.loy || y1 > sc.hiy);
+                    }
+                }
+                const unsigned bal = tm.ballot(ok);
+                if (bal) {
+                    const int win = __ffs(bal) - 1;
+                    if (tm.lane == win) {
+                        S.fx[1] = x1;
+                        S.fy[1] = y1;
+                        S.fth[1] = S.fth[0];
+                    }
+                    first = 2;
+                    break;
+                }
+            }
+            tm.sync();
+        }
+    }
+    for (int i = first; i < N; ++i) {
+        for (int base = 0; base < max_att; base += G) {
+            const int a = base + tm.lane;
+            bool ok = false;
+            float cx = 0.f, cy = 0.f, cth = 0.f;
+            if (a < max_att) {
+                const Words4 v = draw(seed, e, ep, kPos, i, (uint32_t)a);
+                cx = __fadd_rn(sc.lox, __fmul_rn(unit24(v.w[0]), sc.wx));
+                cy = __fadd_rn(sc.loy, __fmul_rn(unit24(v.w[1]), sc.wy));
+                cth = __fadd_rn(-sc.pif, __fmul_rn(unit24(v.w[2]), sc.twopif));
+                ok = true;
+                for (int j = 0; j < i; ++j) {
+                    const float dx = __fsub_rn(cx, S.fx[j]), dy = __fsub_rn(cy, S.fy[j]);
+                    const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                    if (d2 < sc.sep2) { ok = false; break; }
+                }
+            }
+            const unsigned bal = tm.ballot(ok);
+            int writer = -1;
+            if (bal) writer = __ffs(bal) - 1;
+            else if (base + G >= max_att) writer = (max_att - 1) - base;  // keep the last candidate
+            if (writer >= 0) {
+                if (tm.lane == writer) {
+                    S.fx[i] = cx;
+                    S.fy[i] = cy;
+                    S.fth[i] = cth;
+                }
+                break;
+            }
+        }
+        tm.sync();
+    }
+    n_res = 0;
+    if (A.k.scenario == 1) {
+        const Words4 w = draw(seed, e, ep, kNRes, 0, 0u);
+        n_res = A.k.n_res_min + below(w.w[0], (uint32_t)(A.k.n_res_max - A.k.n_res_min + 1));
+        for (int r = tm.lane; r < A.k.r_max; r += G) {
+            if (r < n_res) {
+                const Words4 v = draw(seed, e, ep, kRes, r, 0u);
+                S.qx[r] = (R)__fadd_rn(sc.lox, __fmul_rn(unit24(v.w[0]), sc.wx));
+                S.qy[r] = (R)__fadd_rn(sc.loy, __fmul_rn(unit24(v.w[1]), sc.wy));
+                S.qlevel[r] = 1 + below(v.w[2], 3u);
+                S.qactive[r] = 1;
+            } else {
+                S.qx[r] = (R)0;
+                S.qy[r] = (R)0;
+                S.qlevel[r] = 0;
+                S.qactive[r] = 0;
+            }
+        }
+    }
+    tm.sync();
+}
+
+// Goal and level of robot i for episode ep (owner lane).
+template <typename R>
+__device__ __forceinline__ void robot_goal_level(const LaunchArgs<R>& A, int e, int ep, int i,
+                                                 R& gx, R& gy, int& lv) {
+    const Words4 w = draw(A.seed, e, ep, kGoal, i, 0u);
+    gx = (R)__fadd_rn(A.sc.lox, __fmul_rn(unit24(w.w[0]), A.sc.wx));
+    gy = (R)__fadd_rn(A.sc.loy, __fmul_rn(unit24(w.w[1]), A.sc.wy));
+    lv = 0;
+    if (A.k.scenario == 1) {
+        const Words4 v = draw(A.seed, e, ep, kLevel, i, 0u);
+        lv = 1 + below(v.w[0], 3u);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// One env for T steps
+// ------------------------------------------------------------------------------------------
+template <typename R, int G, int NMAX>
+__device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, NMAX>& S, int e) {
+    constexpr int RPL = (NMAX + G - 1) / G;
+    const StepConsts<R>& k = A.k;
+    const int off = A.s.off[e];
+    const int N = A.s.nrob[e];
+    const bool forage = (k.scenario == 1);
+    QPWork<R, NMAX>& W = WorkSel<R, NMAX>::get(S.qp);
+
+    QPConsts<R> qc;
+    qc.gamma = k.gamma; qc.r2 = k.r2; qc.kg = k.kg; qc.half_r = k.half_r;
+    qc.xmin = k.xmin; qc.xmax = k.xmax; qc.ymin = k.ymin; qc.ymax = k.ymax;
+    qc.h_flag = k.h_flag;
+    qc.max_iter = k.max_iter;
+    if (std::is_same<R, float>::value) {
+        qc.tol_abs = (R)2e-7; qc.tol_rel = (R)1e-6; qc.eps_dep = (R)1e-5; qc.tol_lam = (R)1e-6;
+    } else {
+        qc.tol_abs = (R)1e-12; qc.tol_rel = (R)1e-12; qc.eps_dep = (R)1e-12; qc.tol_lam = (R)1e-10;
+    }
+
+    R x[RPL], y[RPL], th[RPL], gx[RPL], gy[RPL], cs[RPL], sn[RPL];
+    int lv[RPL];
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+        const int i = tm.lane + s * G;
+        x[s] = y[s] = th[s] = gx[s] = gy[s] = cs[s] = sn[s] = (R)0;
+        lv[s] = 0;
+        if (i < N) {
+            x[s] = A.s.x[off + i]; y[s] = A.s.y[off + i]; th[s] = A.s.th[off + i];
+            gx[s] = A.s.gx[off + i]; gy[s] = A.s.gy[off + i]; lv[s] = A.s.level[off + i];
+            sc_(th[s], &sn[s], &cs[s]);
+        }
+    }
+    int t = A.s.t[e], ep = A.s.ep[e];
+    int n_res = 0;
+    if (forage) {
+        n_res = A.s.n_res[e];
+        for (int r = tm.lane; r < k.r_max; r += G) {
+            S.qx[r] = A.s.qx[e * k.r_max + r];
+            S.qy[r] = A.s.qy[e * k.r_max + r];
+            S.qlevel[r] = A.s.qlevel[e * k.r_max + r];
+            S.qactive[r] = A.s.qactive[e * k.r_max + r];
+        }
+    }
+    int cnt[kNCount];
+#pragma unroll
+    for (int c = 0; c < kNCount; ++c) cnt[c] = (tm.lane == 0) ? A.s.counters[e * kNCount + c] : 0;
+    tm.sync();
+
+    for (int step = 0; step < A.T; ++step) {
+        // ---- projected points and nominal SI velocity
+        R dold[RPL], u0x[RPL], u0y[RPL];
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+            const int i = tm.lane + s * G;
+            dold[s] = u0x[s] = u0y[s] = (R)0;
+            if (i < N) {
+                const R px = x[s] + k.l * cs[s], py = y[s] + k.l * sn[s];
+                R ux, uy;
+                if (A.io.actions) {
+                    ux = A.io.actions[2 * (off + i)];
+                    uy = A.io.actions[2 * (off + i) + 1];
+                } else {
+                    R tx = gx[s], ty = gy[s];
+                    if (forage) {
+                        int best = -1;
+                        R bd = (R)0;
+                        for (int r = 0; r < n_res; ++r) {
+                            if (!S.qactive[r]) continue;
+                            const R dx = S.qx[r] - px, dy = S.qy[r] - py;
+                            const R d2 = dx * dx + dy * dy;
+                            if (best < 0 || d2 < bd) { best = r; bd = d2; }
+                        }
+                        if (best >= 0) { tx = S.qx[best]; ty = S.qy[best]; }
+                        else { tx = px; ty = py; }
+                    }
+                    ux = k.k_si * (tx - px);
+                    uy = k.k_si * (ty - py);
+                    cap_norm(ux, uy, k.vmax);
+                    if (k.noise_on) {
+                        const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)t);
+                        const float ex = __fmul_rn(__fsub_rn(unit24(w.w[2 * (i & 1)]), 0.5f), k.noise_scale);
+                        const float ey = __fmul_rn(__fsub_rn(unit24(w.w[2 * (i & 1) + 1]), 0.5f), k.noise_scale);
+                        ux += (R)ex;
+                        uy += (R)ey;
+                    }
+                }
+                cap_norm(ux, uy, k.vmax);
+                u0x[s] = ux;
+                u0y[s] = uy;
+                if (!forage) dold[s] = hyp(px - gx[s], py - gy[s]);
+                W.px[i] = px; W.py[i] = py;
+                W.u0x[i] = ux; W.u0y[i] = uy;
+                W.ux[i] = ux; W.uy[i] = uy;
+            }
+        }
+        tm.sync();
+
+        // ---- barrier-certificate QP
+        QPResult res = qp_solve<R, G, NMAX>(tm, W, N, qc);
+        int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
+        R usx[RPL], usy[RPL];
+        bool resolved = false;
+        if (std::is_same<R, float>::value && k.resolve_f64 && res.flag) {
+            tm.sync();  // every lane is done with the binary32 workspace that D overlays
+            QPWork<double, NMAX>& D = S.qp.d;
+            QPConsts<double> dc;
+            dc.gamma = (double)k.gamma; dc.r2 = (double)k.r2; dc.kg = (double)k.kg;
+            dc.half_r = (double)k.half_r; dc.xmin = (double)k.xmin; dc.xmax = (double)k.xmax;
+            dc.ymin = (double)k.ymin; dc.ymax = (double)k.ymax; dc.h_flag = (double)k.h_flag;
+            dc.max_iter = 8 * NMAX + 16;
+            dc.tol_abs = 1e-12; dc.tol_rel = 1e-12; dc.eps_dep = 1e-12; dc.tol_lam = 1e-10;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                if (i < N) {
+                    double sd, cd;
+                    sincos((double)th[s], &sd, &cd);
+                    D.px[i] = (double)x[s] + (double)k.l * cd;
+                    D.py[i] = (double)y[s] + (double)k.l * sd;
+                    D.u0x[i] = (double)u0x[s];
+                    D.u0y[i] = (double)u0y[s];
+                    D.ux[i] = D.u0x[i];
+                    D.uy[i] = D.u0y[i];
+                }
+            }
+            tm.sync();
+            const QPResult r64 = qp_solve<double, G, NMAX>(tm, D, N, dc);
+            res.status = r64.status;
+            res.q = r64.q;
+            res.iters += r64.iters;
+            resolved = true;
+            qflags |= 2;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                usx[s] = usy[s] = (R)0;
+                if (i < N) { usx[s] = (R)D.ux[i]; usy[s] = (R)D.uy[i]; }
+            }
+        }
+        if (!resolved) {
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                usx[s] = usy[s] = (R)0;
+                if (i < N) { usx[s] = W.ux[i]; usy[s] = W.uy[i]; }
+            }
+        }
+        tm.sync();  // the workspace is reused below
+
+        // ---- SI -> unicycle, wheel clip, Euler step
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+            const int i = tm.lane + s * G;
+            if (i < N) {
+                R v = cs[s] * usx[s] + sn[s] * usy[s];
+                R om = (cs[s] * usy[s] - sn[s] * usx[s]) * k.inv_l;
+                R wr = v + k.half_track * om, wl = v - k.half_track * om;
+                wr = fmin(fmax(wr, -k.vmax), k.vmax);
+                wl = fmin(fmax(wl, -k.vmax), k.vmax);
+                v = (R)0.5 * (wr + wl);
+                om = (wr - wl) * k.inv_track;
+                if (A.io.u_nom) {
+                    A.io.u_nom[2 * (off + i)] = u0x[s];
+                    A.io.u_nom[2 * (off + i) + 1] = u0y[s];
+                }
+                if (A.io.u_star) {
+                    A.io.u_star[2 * (off + i)] = usx[s];
+                    A.io.u_star[2 * (off + i) + 1] = usy[s];
+                }
+                if (A.io.vw) {
+                    A.io.vw[2 * (off + i)] = v;
+                    A.io.vw[2 * (off + i) + 1] = om;
+                }
+                x[s] += k.dt * v * cs[s];
+                y[s] += k.dt * v * sn[s];
+                th[s] = wrap_pi(th[s] + k.dt * om);
+                sc_(th[s], &sn[s], &cs[s]);
+                W.px[i] = x[s] + k.l * cs[s];
+                W.py[i] = y[s] + k.l * sn[s];
+            }
+        }
+        tm.sync();
+
+        // ---- flags and reward
+        int col_l = 0, oob_l = 0;
+        R rew_l = (R)0;
+        const int nd = (N - 1) / 2;
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+            const int i = tm.lane + s * G;
+            if (i < N) {
+                const R pxi = W.px[i], pyi = W.py[i];
+                const int ndi = nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0);
+                for (int d = 1; d <= ndi; ++d) {
+                    int j = i + d;
+                    if (j >= N) j -= N;
+                    const R dx = pxi - W.px[j], dy = pyi - W.py[j];
+                    if (dx * dx + dy * dy < k.r2) ++col_l;
+                }
+                if (pxi < k.xmin || pxi > k.xmax || pyi < k.ymin || pyi > k.ymax) ++oob_l;
+                if (!forage) rew_l -= hyp(pxi - gx[s], pyi - gy[s]) - dold[s];
+            }
+        }
+        const int col = tm.sum(col_l);
+        const int oob = tm.sum(oob_l);
+        R rew = tm.sum(rew_l);
+        bool all_foraged = false;
+        int succ = 0;
+        if (forage) {
+            const R rho2 = k.rho2;
+            int remaining = 0;
+            for (int r = 0; r < n_res; ++r) {
+                const bool act = S.qactive[r] != 0;
+                if (!act) continue;
+                int ls = 0;
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        const R dx = W.px[i] - S.qx[r], dy = W.py[i] - S.qy[r];
+                        if (dx * dx + dy * dy < rho2) ls += lv[s];
+                    }
+                }
+                ls = tm.sum(ls);
+                if (ls >= S.qlevel[r]) {
+                    rew += (R)S.qlevel[r];
+                    ++succ;
+                    tm.sync();
+                    if (tm.lane == 0) S.qactive[r] = 0;
+                    tm.sync();
+                } else {
+                    ++remaining;
+                }
+            }
+            all_foraged = (n_res > 0 && remaining == 0);
+        }
+        rew -= k.c_col * (R)col;
+        if (tm.lane == 0) {
+            cnt[0] += col;
+            cnt[1] += oob;
+            cnt[2] += succ;
+            cnt[3] += (qflags & 1);
+            cnt[4] += (qflags >> 1) & 1;
+            cnt[5] += (res.status == 1) ? 1 : 0;
+            cnt[7] += res.iters;
+        }
+        if (A.io.qp_info && tm.lane == 0) {
+            A.io.qp_info[4 * e + 0] = res.status;
+            A.io.qp_info[4 * e + 1] = res.q;
+            A.io.qp_info[4 * e + 2] = res.iters;
+            A.io.qp_info[4 * e + 3] = qflags;
+        }
+
+        // ---- episode end and auto-reset
+        t += 1;
+        const bool done = (t >= k.episode_len) || all_foraged;
+        if (done) {
+            if (tm.lane == 0) cnt[6] += 1;
+            ep += 1;
+            t = 0;
+            tm.sync();
+            team_sample<R, G, NMAX>(tm, S, A, e, ep, N, n_res);
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                if (i < N) {
+                    x[s] = (R)S.fx[i];
+                    y[s] = (R)S.fy[i];
+                    th[s] = (R)S.fth[i];
+                    sc_(th[s], &sn[s], &cs[s]);
+                    robot_goal_level<R>(A, e, ep, i, gx[s], gy[s], lv[s]);
+                }
+            }
+            tm.sync();
+        }
+
+        // ---- observations
+        if (A.io.obs) {
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                if (i < N) {
+                    S.sx[i] = x[s]; S.sy[i] = y[s]; S.sth[i] = th[s]; S.slevel[i] = lv[s];
+                }
+            }
+            tm.sync();
+            const int od = A.io.obs_dim;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                if (i < N) {
+                    R* o = A.io.obs + (long long)step * A.io.obs_step + (long long)(off + i) * od;
+                    int c = 0;
+                    if (!forage) {
+                        o[0] = x[s]; o[1] = y[s]; o[2] = th[s]; o[3] = gx[s]; o[4] = gy[s];
+                        c = 5;
+                        for (int j = 0; j < N; ++j) {
+                            if (j == i) continue;
+                            o[c] = S.sx[j] - x[s];
+                            o[c + 1] = S.sy[j] - y[s];
+                            o[c + 2] = wrap_pi(S.sth[j] - th[s]);
+                            c += 3;
+                        }
+                        for (; c < od; ++c) o[c] = (R)0;
+                    } else {
+                        o[0] = x[s]; o[1] = y[s]; o[2] = th[s]; o[3] = (R)lv[s];
+                        c = 4;
+                        for (int j = 0; j < N; ++j) {
+                            if (j == i) continue;
+                            o[c] = S.sx[j] - x[s];
+                            o[c + 1] = S.sy[j] - y[s];
+                            o[c + 2] = wrap_pi(S.sth[j] - th[s]);
+                            o[c + 3] = (R)S.slevel[j];
+                            c += 4;
+                        }
+                        const int rbase = 4 + 4 * (k.n_max_obs - 1);
+                        for (; c < rbase; ++c) o[c] = (R)0;
+                        for (int r = 0; r < k.r_max; ++r) {
+                            if (r < n_res) {
+                                o[c] = S.qx[r] - x[s];
+                                o[c + 1] = S.qy[r] - y[s];
+                                o[c + 2] = (R)S.qlevel[r];
+                                o[c + 3] = (R)S.qactive[r];
+                            } else {
+                                o[c] = o[c + 1] = o[c + 2] = o[c + 3] = (R)0;
+                            }
+                            c += 4;
+                        }
+                    }
+                }
+            }
+            tm.sync();
+        }
+        if (tm.lane == 0) {
+            if (A.io.reward) A.io.reward[(long long)step * A.io.E + e] = rew;
+            if (A.io.done) A.io.done[(long long)step * A.io.E + e] = done ? 1 : 0;
+        }
+    }
+
+    // ---- state back to global memory
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+        const int i = tm.lane + s * G;
+        if (i < N) {
+            A.s.x[off + i] = x[s]; A.s.y[off + i] = y[s]; A.s.th[off + i] = th[s];
+            A.s.gx[off + i] = gx[s]; A.s.gy[off + i] = gy[s]; A.s.level[off + i] = lv[s];
+        }
+    }
+    if (forage) {
+        for (int r = tm.lane; r < k.r_max; r += G) {
+            A.s.qx[e * k.r_max + r] = S.qx[r];
+            A.s.qy[e * k.r_max + r] = S.qy[r];
+            A.s.qlevel[e * k.r_max + r] = S.qlevel[r];
+            A.s.qactive[e * k.r_max + r] = S.qactive[r];
+        }
+    }
+    if (tm.lane == 0) {
+        A.s.t[e] = t;
+        A.s.ep[e] = ep;
+        if (forage) A.s.n_res[e] = n_res;
+#pragma unroll
+        for (int c = 0; c < kNCount; ++c) A.s.counters[e * kNCount + c] = cnt[c];
+    }
+}
+
+// Reset env e to episode ep (state written to global memory).
+template <typename R, int G, int NMAX>
+__device__ void reset_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, NMAX>& S, int e,
+                          int ep) {
+    constexpr int RPL = (NMAX + G - 1) / G;
+    const int off = A.s.off[e];
+    const int N = A.s.nrob[e];
+    int n_res = 0;
+    team_sample<R, G, NMAX>(tm, S, A, e, ep, N, n_res);
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+        const int i = tm.lane + s * G;
+        if (i < N) {
+            R gx, gy;
+            int lv;
+            robot_goal_level<R>(A, e, ep, i, gx, gy, lv);
+            A.s.x[off + i] = (R)S.fx[i];
+            A.s.y[off + i] = (R)S.fy[i];
+            A.s.th[off + i] = (R)S.fth[i];
+            A.s.gx[off + i] = gx;
+            A.s.gy[off + i] = gy;
+            A.s.level[off + i] = lv;
+        }
+    }
+    if (A.k.scenario == 1) {
+        for (int r = tm.lane; r < A.k.r_max; r += G) {
+            A.s.qx[e * A.k.r_max + r] = S.qx[r];
+            A.s.qy[e * A.k.r_max + r] = S.qy[r];
+            A.s.qlevel[e * A.k.r_max + r] = S.qlevel[r];
+            A.s.qactive[e * A.k.r_max + r] = S.qactive[r];
+        }
+    }
+    if (tm.lane == 0) {
+        A.s.t[e] = 0;
+        A.s.ep[e] = ep;
+        A.s.n_res[e] = n_res;
+        for (int c = 0; c < kNCount; ++c) A.s.counters[e * kNCount + c] = 0;
+    }
+    tm.sync();
+}
+
+template <typename R, int G, int NMAX>
+__global__ void __launch_bounds__(256) env_kernel(LaunchArgs<R> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Team<G> tm;
+    const int teams_per_block = blockDim.x / G;
+    const int tib = threadIdx.x / G;
+    TeamSmem<R, NMAX>* S = reinterpret_cast<TeamSmem<R, NMAX>*>(smem_raw) + tib;
+    const int total_teams = gridDim.x * teams_per_block;
+    for (int idx = blockIdx.x * teams_per_block + tib; idx < A.n_list; idx += total_teams) {
+        const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
+        run_env<R, G, NMAX>(A, tm, *S, e);
+    }
+}
+
+template <typename R, int G, int NMAX>
+__global__ void __launch_bounds__(256) reset_kernel(LaunchArgs<R> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Team<G> tm;
+    const int teams_per_block = blockDim.x / G;
+    const int tib = threadIdx.x / G;
+    TeamSmem<R, NMAX>* S = reinterpret_cast<TeamSmem<R, NMAX>*>(smem_raw) + tib;
+    const int total_teams = gridDim.x * teams_per_block;
+    for (int idx = blockIdx.x * teams_per_block + tib; idx < A.n_list; idx += total_teams) {
+        const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
+        reset_env<R, G, NMAX>(A, tm, *S, e, 0);
+    }
+}
+
+}  // namespace rl

@@ -1,0 +1,47 @@
+// launch.h -- host-side launchers of the environment kernels (one translation unit per
+// precision / size class so that the library builds in parallel).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "env_step.cuh"
+
+namespace rl {
+
+// Robot-count classes: an env with n robots runs in the smallest class with n <= nmax.
+constexpr int kClassNmax[4] = {4, 8, 16, 32};
+
+// Launch the step (reset == false) or reset (reset == true) kernel of one class.
+// lanes: team size; block_threads: a multiple of 32; max_blocks <= 0: one team per env.
+cudaError_t launch_f32_small(const LaunchArgs<float>& a, int lanes, int block_threads,
+                             int max_blocks, cudaStream_t st, bool reset);
+cudaError_t launch_f32_large(const LaunchArgs<float>& a, int nmax, int lanes, int block_threads,
+                             int max_blocks, cudaStream_t st, bool reset);
+cudaError_t launch_f64(const LaunchArgs<double>& a, int nmax, int lanes, int block_threads,
+                       int max_blocks, cudaStream_t st, bool reset);
+
+// Shared memory per team of a class.
+size_t team_smem_bytes(int precision, int nmax);
+// Lanes a class supports (bitmask of powers of two).
+unsigned supported_lanes(int precision, int nmax);
+
+template <typename R, int G, int NMAX>
+cudaError_t launch_one(const LaunchArgs<R>& a, int block_threads, int max_blocks,
+                       cudaStream_t st, bool reset) {
+    if (block_threads < G || block_threads % 32 != 0 || block_threads > 256)
+        return cudaErrorInvalidValue;
+    const int tpb = block_threads / G;
+    const size_t smem = (size_t)tpb * sizeof(TeamSmem<R, NMAX>);
+    void (*kern)(LaunchArgs<R>) = reset ? reset_kernel<R, G, NMAX> : env_kernel<R, G, NMAX>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int blocks = (a.n_list + tpb - 1) / tpb;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+    if (blocks <= 0) return cudaSuccess;
+    kern<<<blocks, block_threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace rl

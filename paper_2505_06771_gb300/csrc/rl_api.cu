@@ -1,0 +1,556 @@
+// rl_api.cu -- the C ABI of include/rl.h: handles, device state, launches, CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rl.h"
+#include "launch.h"
+
+namespace {
+
+constexpr uint32_t kMagic = 0x31534C52u;  // "RLS1"
+constexpr uint32_t kVersion = 1u;
+constexpr int kSegs = 16;
+enum Seg { S_X = 0, S_Y, S_TH, S_GX, S_GY, S_LEVEL, S_T, S_EP, S_NRES, S_QX, S_QY, S_QLEVEL,
+           S_QACTIVE, S_COUNTERS, S_NROB, S_OFF };
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t precision, scenario, n_envs, total_robots, r_max, n_max;
+    uint64_t seed, image_bytes;
+    uint8_t pad[16];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+
+struct Class {
+    int nmax, lanes, begin, count, block_threads;
+};
+
+}  // namespace
+
+struct rl_env {
+    rl_config cfg;
+    int E = 0, total = 0, n_max = 0, r_max = 0, obs_dim = 0, prec = 32, esz = 4;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    uint64_t seed = 0;
+    unsigned char* d_img = nullptr;
+    size_t img_bytes = 0;
+    size_t seg_off[kSegs] = {};
+    size_t seg_len[kSegs] = {};
+    int32_t* d_lists = nullptr;
+    std::vector<int32_t> h_nrob, h_off;
+    Class cls[4];
+    int ncls = 0;
+    std::string err;
+    // rollout graph cache
+    cudaGraphExec_t gexec = nullptr;
+    int g_T = -1;
+    void *g_obs = nullptr, *g_rew = nullptr;
+    uint8_t* g_done = nullptr;
+    // device scratch of rl_rollout_host
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace {
+
+rl_status fail(rl_env* h, rl_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+rl_status cuda_fail(rl_env* h, cudaError_t e, const char* where) {
+    return fail(h, RL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_cfg(const rl_config& c, std::string& why) {
+    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING) { why = "scenario"; return false; }
+    if (c.precision != RL_PREC_F32 && c.precision != RL_PREC_F64) { why = "precision"; return false; }
+    if (c.episode_len < 1) { why = "episode_len"; return false; }
+    if (c.max_attempts < 1) { why = "max_attempts"; return false; }
+    if (!(c.l > 0) || !(c.vmax > 0) || !(c.wmax > 0) || !(c.dt > 0) || !(c.r >= 0)) { why = "constants"; return false; }
+    if (!(c.xmax > c.xmin) || !(c.ymax > c.ymin)) { why = "arena"; return false; }
+    if (c.scenario == RL_SCEN_FORAGING) {
+        if (c.r_max < 1 || c.r_max > rl::kMaxRes) { why = "r_max"; return false; }
+        if (c.n_res_min < 0 || c.n_res_max > c.r_max || c.n_res_min > c.n_res_max) { why = "n_res"; return false; }
+    }
+    if (c.n_max < 0 || c.n_max > rl::kMaxRobots) { why = "n_max"; return false; }
+    return true;
+}
+
+template <typename R>
+void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
+    const rl_config& c = h->cfg;
+    auto seg = [&](int s) { return (void*)(h->d_img + h->seg_off[s]); };
+    a.s.x = (R*)seg(S_X); a.s.y = (R*)seg(S_Y); a.s.th = (R*)seg(S_TH);
+    a.s.gx = (R*)seg(S_GX); a.s.gy = (R*)seg(S_GY);
+    a.s.level = (int32_t*)seg(S_LEVEL);
+    a.s.t = (int32_t*)seg(S_T); a.s.ep = (int32_t*)seg(S_EP); a.s.n_res = (int32_t*)seg(S_NRES);
+    a.s.qx = (R*)seg(S_QX); a.s.qy = (R*)seg(S_QY);
+    a.s.qlevel = (int32_t*)seg(S_QLEVEL); a.s.qactive = (int32_t*)seg(S_QACTIVE);
+    a.s.counters = (int32_t*)seg(S_COUNTERS);
+    a.s.off = (const int32_t*)seg(S_OFF);
+    a.s.nrob = (const int32_t*)seg(S_NROB);
+    std::memset(&a.io, 0, sizeof(a.io));
+    a.io.E = h->E;
+    a.io.obs_dim = h->obs_dim;
+    a.io.obs_step = (long long)h->total * h->obs_dim;
+    rl::StepConsts<R>& k = a.k;
+    const double track = 2.0 * c.vmax / c.wmax;
+    k.gamma = (R)c.gamma; k.r2 = (R)(c.r * c.r); k.l = (R)c.l; k.inv_l = (R)(1.0 / c.l);
+    k.vmax = (R)c.vmax; k.half_track = (R)(0.5 * track); k.inv_track = (R)(1.0 / track);
+    k.dt = (R)c.dt; k.kg = (R)(c.kappa * c.gamma); k.half_r = (R)(0.5 * c.r); k.k_si = (R)c.k_si;
+    k.c_col = (R)c.c_col; k.rho2 = (R)(c.forage_radius * c.forage_radius);
+    k.xmin = (R)c.xmin; k.xmax = (R)c.xmax; k.ymin = (R)c.ymin; k.ymax = (R)c.ymax;
+    k.h_flag = (R)c.h_flag;
+    k.scenario = c.scenario; k.scripted = c.scripted; k.episode_len = c.episode_len;
+    k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * h->n_max + 16;
+    k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = h->r_max;
+    k.n_max_obs = h->n_max; k.max_attempts = c.max_attempts; k.resolve_f64 = c.resolve_f64;
+    k.noise_on = c.noise_amp > 0.0 ? 1 : 0;
+    k.noise_scale = 2.0f * (float)c.noise_amp;
+    rl::SamplerConsts& s = a.sc;
+    s.lox = (float)c.xmin + (float)c.init_margin;
+    s.hix = (float)c.xmax - (float)c.init_margin;
+    s.loy = (float)c.ymin + (float)c.init_margin;
+    s.hiy = (float)c.ymax - (float)c.init_margin;
+    s.wx = s.hix - s.lox;
+    s.wy = s.hiy - s.loy;
+    s.sep2 = (float)c.min_sep * (float)c.min_sep;
+    s.pif = (float)M_PI;
+    s.twopif = (float)(2.0 * M_PI);
+    s.near_frac = (float)c.near_frac;
+    s.dmin = (float)c.near_dmin;
+    s.dspan = (float)c.near_dmax - (float)c.near_dmin;
+    s.near_on = c.near_frac > 0.0 ? 1 : 0;
+    a.env_list = nullptr;
+    a.n_list = 0;
+    a.env_begin = 0;
+    a.T = 1;
+    a.seed = h->seed;
+}
+
+template <typename R>
+cudaError_t launch_class(const rl_env* h, const Class& c, rl::LaunchArgs<R> a, bool reset,
+                         int max_blocks = 0) {
+    a.env_list = h->d_lists + c.begin;
+    a.n_list = c.count;
+    if constexpr (std::is_same<R, double>::value) {
+        return rl::launch_f64(a, c.nmax, c.lanes, c.block_threads, max_blocks, h->st, reset);
+    } else {
+        if (c.nmax == 4)
+            return rl::launch_f32_small(a, c.lanes, c.block_threads, max_blocks, h->st, reset);
+        return rl::launch_f32_large(a, c.nmax, c.lanes, c.block_threads, max_blocks, h->st, reset);
+    }
+}
+
+template <typename R>
+rl_status run_all(rl_env* h, rl::LaunchArgs<R>& a, bool reset, const char* what) {
+    for (int i = 0; i < h->ncls; ++i) {
+        cudaError_t e = launch_class<R>(h, h->cls[i], a, reset);
+        if (e != cudaSuccess) return cuda_fail(h, e, what);
+    }
+    return RL_OK;
+}
+
+rl_status do_reset(rl_env* h) {
+    if (h->prec == 64) {
+        rl::LaunchArgs<double> a;
+        fill_args(h, a);
+        return run_all(h, a, true, "reset");
+    }
+    rl::LaunchArgs<float> a;
+    fill_args(h, a);
+    return run_all(h, a, true, "reset");
+}
+
+template <typename R>
+rl_status do_step(rl_env* h, const rl_step_io* io) {
+    rl::LaunchArgs<R> a;
+    fill_args(h, a);
+    a.T = 1;
+    a.io.actions = (const R*)io->d_actions;
+    a.io.obs = (R*)io->d_obs;
+    a.io.reward = (R*)io->d_reward;
+    a.io.done = io->d_done;
+    a.io.u_nom = (R*)io->d_u_nom;
+    a.io.u_star = (R*)io->d_u_star;
+    a.io.vw = (R*)io->d_vw;
+    a.io.qp_info = io->d_qp_info;
+    return run_all(h, a, false, "step");
+}
+
+template <typename R>
+rl_status do_rollout_launch(rl_env* h, int T, void* obs, void* rew, uint8_t* done) {
+    rl::LaunchArgs<R> a;
+    fill_args(h, a);
+    a.T = T;
+    a.io.obs = (R*)obs;
+    a.io.reward = (R*)rew;
+    a.io.done = done;
+    return run_all(h, a, false, "rollout");
+}
+
+rl_status rollout_enqueue(rl_env* h, int T, void* obs, void* rew, uint8_t* done) {
+    return h->prec == 64 ? do_rollout_launch<double>(h, T, obs, rew, done)
+                         : do_rollout_launch<float>(h, T, obs, rew, done);
+}
+
+void drop_graph(rl_env* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_T = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+rl_status rl_config_default(int32_t scenario, rl_config* out) {
+    if (!out) return RL_ERR_ARG;
+    if (scenario != RL_SCEN_NAVIGATION && scenario != RL_SCEN_FORAGING) return RL_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->scenario = scenario;
+    out->precision = RL_PREC_F32;
+    out->scripted = 1;
+    out->episode_len = 100;
+    out->n_res_min = 2;
+    out->n_res_max = 6;
+    out->r_max = scenario == RL_SCEN_FORAGING ? 6 : 0;
+    out->n_max = 0;
+    out->max_attempts = 4096;
+    out->qp_max_iter = 0;
+    out->resolve_f64 = 1;
+    out->lanes = 0;
+    out->gamma = 100.0;
+    out->r = 0.17;
+    out->l = 0.05;
+    out->vmax = 0.2;
+    out->wmax = 3.6;
+    out->dt = 0.033;
+    out->kappa = 0.4;
+    out->k_si = 1.0;
+    out->noise_amp = 0.05;
+    out->c_col = scenario == RL_SCEN_NAVIGATION ? 1.0 : 0.0;
+    out->forage_radius = 0.25;
+    out->xmin = -1.6;
+    out->xmax = 1.6;
+    out->ymin = -1.0;
+    out->ymax = 1.0;
+    out->init_margin = 0.2;
+    out->min_sep = 0.3;
+    out->near_frac = 0.0;
+    out->near_dmin = 0.18;
+    out->near_dmax = 0.20;
+    out->h_flag = 1e-3;
+    return RL_OK;
+}
+
+rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_robots,
+                    int32_t n_robots_uniform, uint64_t seed, void* stream, rl_env** out) {
+    if (!cfg || !out || n_envs < 1) return RL_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    if (!valid_cfg(*cfg, why)) return RL_ERR_ARG;
+    rl_env* h = new (std::nothrow) rl_env();
+    if (!h) return RL_ERR_OOM;
+    h->cfg = *cfg;
+    h->E = n_envs;
+    h->prec = cfg->precision;
+    h->esz = cfg->precision == 64 ? 8 : 4;
+    h->seed = seed;
+    h->h_nrob.resize(n_envs);
+    h->h_off.resize(n_envs + 1);
+    int nmax_seen = 0;
+    h->h_off[0] = 0;
+    for (int e = 0; e < n_envs; ++e) {
+        const int n = h_n_robots ? h_n_robots[e] : n_robots_uniform;
+        if (n < 1 || n > rl::kMaxRobots) { delete h; return RL_ERR_ARG; }
+        h->h_nrob[e] = n;
+        h->h_off[e + 1] = h->h_off[e] + n;
+        nmax_seen = std::max(nmax_seen, n);
+    }
+    h->total = h->h_off[n_envs];
+    h->n_max = cfg->n_max > 0 ? cfg->n_max : nmax_seen;
+    if (h->n_max < nmax_seen) { delete h; return RL_ERR_ARG; }
+    h->r_max = cfg->scenario == RL_SCEN_FORAGING ? cfg->r_max : 0;
+    h->obs_dim = cfg->scenario == RL_SCEN_FORAGING ? 4 + 4 * (h->n_max - 1) + 4 * h->r_max
+                                                   : 5 + 3 * (h->n_max - 1);
+    // segments of the state image
+    const size_t E = (size_t)n_envs, T = (size_t)h->total, RM = (size_t)h->r_max * E;
+    const size_t lens[kSegs] = {T * h->esz, T * h->esz, T * h->esz, T * h->esz, T * h->esz,
+                                T * 4, E * 4, E * 4, E * 4, RM * h->esz, RM * h->esz, RM * 4,
+                                RM * 4, E * rl::kNCount * 4, E * 4, (E + 1) * 4};
+    size_t pos = 0;
+    for (int s = 0; s < kSegs; ++s) {
+        h->seg_off[s] = pos;
+        h->seg_len[s] = lens[s];
+        pos += (lens[s] + 255) & ~(size_t)255;
+    }
+    h->img_bytes = pos;
+    if (stream) {
+        h->st = (cudaStream_t)stream;
+    } else {
+        // a blocking stream: ordered with the legacy default stream, as the caller expects
+        cudaError_t e = cudaStreamCreate(&h->st);
+        if (e != cudaSuccess) { delete h; return RL_ERR_CUDA; }
+        h->own_stream = true;
+    }
+    if (cudaMalloc((void**)&h->d_img, h->img_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        rl_destroy(h);
+        return RL_ERR_OOM;
+    }
+    // classes by robot count
+    std::vector<int32_t> lists;
+    for (int c = 0; c < 4; ++c) {
+        const int nm = rl::kClassNmax[c];
+        const int lo = c == 0 ? 1 : rl::kClassNmax[c - 1] + 1;
+        Class k;
+        k.nmax = nm;
+        k.begin = (int)lists.size();
+        for (int e = 0; e < n_envs; ++e)
+            if (h->h_nrob[e] >= lo && h->h_nrob[e] <= nm) lists.push_back(e);
+        k.count = (int)lists.size() - k.begin;
+        if (k.count == 0) continue;
+        const unsigned ok = rl::supported_lanes(h->prec, nm);
+        int lanes = cfg->lanes > 0 ? cfg->lanes : nm;
+        if (!(lanes > 0 && (ok & (unsigned)lanes))) lanes = nm;
+        k.lanes = lanes;
+        k.block_threads = nm <= 8 ? 64 : (nm == 16 ? 64 : 32);
+        h->cls[h->ncls++] = k;
+    }
+    cudaError_t ce = cudaMalloc((void**)&h->d_lists, lists.size() * sizeof(int32_t));
+    if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
+    ce = cudaMemsetAsync(h->d_img, 0, h->img_bytes, h->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(h->d_lists, lists.data(), lists.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, h->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(h->d_img + h->seg_off[S_NROB], h->h_nrob.data(), E * 4,
+                             cudaMemcpyHostToDevice, h->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(h->d_img + h->seg_off[S_OFF], h->h_off.data(), (E + 1) * 4,
+                             cudaMemcpyHostToDevice, h->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
+    if (ce != cudaSuccess) { rl_destroy(h); return RL_ERR_CUDA; }
+    rl_status s = do_reset(h);
+    if (s != RL_OK) { rl_destroy(h); return s; }
+    *out = h;
+    return RL_OK;
+}
+
+rl_status rl_reset(rl_env* h, uint64_t seed) {
+    if (!h) return RL_ERR_ARG;
+    h->seed = seed;
+    drop_graph(h);
+    return do_reset(h);
+}
+
+rl_status rl_step_io_call(rl_env* h, const rl_step_io* io) {
+    if (!h || !io) return RL_ERR_ARG;
+    if (!h->cfg.scripted && !io->d_actions)
+        return fail(h, RL_ERR_ARG, "rl_step: actions are required for a policy-driven handle");
+    if (h->cfg.scripted && io->d_actions)
+        return fail(h, RL_ERR_ARG, "rl_step: a scripted handle takes no actions");
+    return h->prec == 64 ? do_step<double>(h, io) : do_step<float>(h, io);
+}
+
+rl_status rl_step(rl_env* h, const void* d_actions, void* d_obs, void* d_reward,
+                  uint8_t* d_done) {
+    rl_step_io io;
+    std::memset(&io, 0, sizeof(io));
+    io.d_actions = d_actions;
+    io.d_obs = d_obs;
+    io.d_reward = d_reward;
+    io.d_done = d_done;
+    return rl_step_io_call(h, &io);
+}
+
+rl_status rl_rollout(rl_env* h, int32_t T, void* d_obs, void* d_rew, uint8_t* d_done) {
+    if (!h || T < 0) return RL_ERR_ARG;
+    if (!h->cfg.scripted) return fail(h, RL_ERR_STATE, "rl_rollout: the handle takes policy actions");
+    if (T == 0) return RL_OK;
+    if (!(h->gexec && h->g_T == T && h->g_obs == d_obs && h->g_rew == d_rew &&
+          h->g_done == d_done)) {
+        drop_graph(h);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(h, e, "rollout capture");
+        rl_status s = rollout_enqueue(h, T, d_obs, d_rew, d_done);
+        e = cudaStreamEndCapture(h->st, &g);
+        if (s != RL_OK) { if (g) cudaGraphDestroy(g); return s; }
+        if (e != cudaSuccess) return cuda_fail(h, e, "rollout capture");
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+        h->g_T = T;
+        h->g_obs = d_obs;
+        h->g_rew = d_rew;
+        h->g_done = d_done;
+    }
+    cudaError_t e = cudaGraphLaunch(h->gexec, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    return RL_OK;
+}
+
+rl_status rl_rollout_plain(rl_env* h, int32_t T, void* d_obs, void* d_rew, uint8_t* d_done) {
+    if (!h || T < 0) return RL_ERR_ARG;
+    if (!h->cfg.scripted) return fail(h, RL_ERR_STATE, "rl_rollout_plain: the handle takes policy actions");
+    const size_t ostep = (size_t)h->total * h->obs_dim * h->esz;
+    for (int t = 0; t < T; ++t) {
+        for (int c = 0; c < h->ncls; ++c) {
+            Class one = h->cls[c];
+            for (int i = 0; i < h->cls[c].count; ++i) {
+                one.begin = h->cls[c].begin + i;
+                one.count = 1;
+                one.block_threads = 32 > one.lanes ? 32 : one.lanes;
+                cudaError_t e;
+                void* o = d_obs ? (char*)d_obs + t * ostep : nullptr;
+                if (h->prec == 64) {
+                    rl::LaunchArgs<double> a;
+                    fill_args(h, a);
+                    a.io.obs = (double*)o;
+                    a.io.reward = d_rew ? (double*)d_rew + (size_t)t * h->E : nullptr;
+                    a.io.done = d_done ? d_done + (size_t)t * h->E : nullptr;
+                    e = launch_class<double>(h, one, a, false);
+                } else {
+                    rl::LaunchArgs<float> a;
+                    fill_args(h, a);
+                    a.io.obs = (float*)o;
+                    a.io.reward = d_rew ? (float*)d_rew + (size_t)t * h->E : nullptr;
+                    a.io.done = d_done ? d_done + (size_t)t * h->E : nullptr;
+                    e = launch_class<float>(h, one, a, false);
+                }
+                if (e != cudaSuccess) return cuda_fail(h, e, "plain step");
+            }
+        }
+    }
+    return RL_OK;
+}
+
+size_t rl_state_bytes(const rl_env* h) { return h ? sizeof(StateHeader) + h->img_bytes : 0; }
+
+rl_status rl_get_state(rl_env* h, void* dst, size_t bytes) {
+    if (!h || !dst || bytes < rl_state_bytes(h)) return RL_ERR_ARG;
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    hd.magic = kMagic;
+    hd.version = kVersion;
+    hd.precision = h->prec;
+    hd.scenario = h->cfg.scenario;
+    hd.n_envs = h->E;
+    hd.total_robots = h->total;
+    hd.r_max = h->r_max;
+    hd.n_max = h->n_max;
+    hd.seed = h->seed;
+    hd.image_bytes = h->img_bytes;
+    std::memcpy(dst, &hd, sizeof(hd));
+    cudaError_t e = cudaMemcpyAsync((char*)dst + sizeof(hd), h->d_img, h->img_bytes,
+                                    cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+    return RL_OK;
+}
+
+rl_status rl_set_state(rl_env* h, const void* src, size_t bytes) {
+    if (!h || !src || bytes < rl_state_bytes(h)) return RL_ERR_ARG;
+    StateHeader hd;
+    std::memcpy(&hd, src, sizeof(hd));
+    if (hd.magic != kMagic || hd.version != kVersion || hd.precision != h->prec ||
+        hd.scenario != h->cfg.scenario || hd.n_envs != h->E || hd.total_robots != h->total ||
+        hd.r_max != h->r_max || hd.image_bytes != h->img_bytes)
+        return fail(h, RL_ERR_ARG, "set_state: the blob does not match this handle");
+    const char* img = (const char*)src + sizeof(hd);
+    if (std::memcmp(img + h->seg_off[S_NROB], h->h_nrob.data(), h->E * 4) != 0 ||
+        std::memcmp(img + h->seg_off[S_OFF], h->h_off.data(), (h->E + 1) * 4) != 0)
+        return fail(h, RL_ERR_ARG, "set_state: robot counts differ from this handle");
+    h->seed = hd.seed;
+    cudaError_t e = cudaMemcpyAsync(h->d_img, img, h->img_bytes, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+    drop_graph(h);
+    return RL_OK;
+}
+
+rl_status rl_rollout_host(rl_env* h, const void* h_state, int32_t T, void* h_obs, void* h_rew,
+                          uint8_t* h_done) {
+    if (!h || T < 0) return RL_ERR_ARG;
+    if (h_state) {
+        StateHeader hd;
+        std::memcpy(&hd, h_state, sizeof(hd));
+        if (hd.magic != kMagic || hd.image_bytes != h->img_bytes)
+            return fail(h, RL_ERR_ARG, "rollout_host: bad state blob");
+        const char* img = (const char*)h_state + sizeof(hd);
+        cudaError_t e = cudaMemcpyAsync(h->d_img, img, h->img_bytes, cudaMemcpyHostToDevice, h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "rollout_host upload");
+    }
+    const size_t ob = h_obs ? (size_t)T * h->total * h->obs_dim * h->esz : 0;
+    const size_t rb = h_rew ? (size_t)T * h->E * h->esz : 0;
+    const size_t db = h_done ? (size_t)T * h->E : 0;
+    const size_t need = ((ob + 255) & ~(size_t)255) + ((rb + 255) & ~(size_t)255) + db + 256;
+    if (need > h->scratch_bytes) {
+        if (h->d_scratch) { cudaFree(h->d_scratch); h->d_scratch = nullptr; h->scratch_bytes = 0; }
+        drop_graph(h);
+        if (cudaMalloc(&h->d_scratch, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, RL_ERR_OOM, "rollout_host: scratch allocation");
+        }
+        h->scratch_bytes = need;
+    }
+    char* base = (char*)h->d_scratch;
+    void* d_obs = h_obs ? base : nullptr;
+    void* d_rew = h_rew ? base + ((ob + 255) & ~(size_t)255) : nullptr;
+    uint8_t* d_done = h_done ? (uint8_t*)(base + ((ob + 255) & ~(size_t)255) + ((rb + 255) & ~(size_t)255)) : nullptr;
+    rl_status s = rl_rollout(h, T, d_obs, d_rew, d_done);
+    if (s != RL_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (h_obs) e = cudaMemcpyAsync(h_obs, d_obs, ob, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h_rew) e = cudaMemcpyAsync(h_rew, d_rew, rb, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h_done) e = cudaMemcpyAsync(h_done, d_done, db, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rollout_host download");
+    return RL_OK;
+}
+
+rl_status rl_get_counters(rl_env* h, int32_t* dst) {
+    if (!h || !dst) return RL_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(dst, h->d_img + h->seg_off[S_COUNTERS],
+                                    h->seg_len[S_COUNTERS], cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_counters");
+    return RL_OK;
+}
+
+rl_status rl_sync(rl_env* h) {
+    if (!h) return RL_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    return RL_OK;
+}
+
+int32_t rl_obs_dim(const rl_env* h) { return h ? h->obs_dim : 0; }
+int32_t rl_n_envs(const rl_env* h) { return h ? h->E : 0; }
+int32_t rl_total_robots(const rl_env* h) { return h ? h->total : 0; }
+int32_t rl_lanes(const rl_env* h) { return (h && h->ncls > 0) ? h->cls[0].lanes : 0; }
+const char* rl_last_error(const rl_env* h) { return h ? h->err.c_str() : "null handle"; }
+
+void rl_destroy(rl_env* h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    drop_graph(h);
+    if (h->d_scratch) cudaFree(h->d_scratch);
+    if (h->d_lists) cudaFree(h->d_lists);
+    if (h->d_img) cudaFree(h->d_img);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Bars: integer outputs (done flags, counters, levels, resource states, sampled initial states)
+bit-exact; binary64 GPU path within 1e-9 of the oracle; binary32 path: filtered controls within
+1e-5 per step (teacher-forced: both sides step from the same state), poses within 1e-4 after
+100 free-running steps.  Max errors are printed per case.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from pairing import make_pair, obs_diff, to_oracle_state, wrap
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_TOL = 1e-5      # filtered SI velocity, binary32
+POSE_TOL = 1e-4   # poses after 100 free-running steps, binary32
+
+
+@pytest.fixture(scope="module")
+def rl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2505_06771_gb300 as m
+    m.build()
+    return m
+
+
+def _alloc(env, T=None):
+    dt = env.dtype
+    R, E, od = env.total_robots, env.n_envs, env.obs_dim
+    if T is None:
+        return dict(obs=torch.zeros(R, od, dtype=dt, device="cuda"),
+                    reward=torch.zeros(E, dtype=dt, device="cuda"),
+                    done=torch.zeros(E, dtype=torch.uint8, device="cuda"),
+                    u_nom=torch.zeros(R, 2, dtype=dt, device="cuda"),
+                    u_star=torch.zeros(R, 2, dtype=dt, device="cuda"),
+                    vw=torch.zeros(R, 2, dtype=dt, device="cuda"),
+                    qp_info=torch.zeros(E, 4, dtype=torch.int32, device="cuda"))
+    return dict(obs=torch.zeros(T, R, od, dtype=dt, device="cuda"),
+                reward=torch.zeros(T, E, dtype=dt, device="cuda"),
+                done=torch.zeros(T, E, dtype=torch.uint8, device="cuda"))
+
+
+def _check_reset_state(g, o, st, n_robots, seed):
+    s = oracle.reset(o, seed, n_robots)
+    for k in ("x", "y", "th", "gx", "gy"):
+        assert np.array_equal(st[k].astype(np.float64), getattr(s, k)), k
+    assert np.array_equal(st["level"], s.level)
+    assert np.array_equal(st["n_res"], s.n_res)
+    if o["r_max"] > 0:
+        assert np.array_equal(st["qx"].astype(np.float64), s.qx)
+        assert np.array_equal(st["qlevel"], s.qlevel)
+        assert np.array_equal(st["qactive"], s.qactive)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("case", ["nav4", "nav20_near", "forage_uneven", "nav_edge"])
+def test_reset_sampler_bit_exact(rl, prec, case):
+    if case == "nav4":
+        g, o = make_pair(0, 4, prec)
+        n = [4] * 300
+    elif case == "nav20_near":
+        g, o = make_pair(0, 20, prec, near_frac=0.3)
+        n = [20] * 64
+    elif case == "forage_uneven":
+        g, o = make_pair(1, 10, prec)
+        n = list(np.random.default_rng(5).integers(2, 11, 257))
+    else:
+        g, o = make_pair(0, 32, prec)
+        n = [1, 2, 3, 5, 8, 9, 16, 17, 31, 32, 4]
+    seed = 0xC0FFEE
+    env = rl.Env(g, len(n), n, seed)
+    _check_reset_state(g, o, env.state_arrays(), n, seed)
+    env.close()
+
+
+def _teacher_forced(rl, g, o, n, seed, steps, actions=False):
+    env = rl.Env(g, len(n), n, seed)
+    b = _alloc(env)
+    err = dict(u_nom=0.0, u_star=0.0, v=0.0, w=0.0, pose=0.0, th=0.0, rew=0.0, obs=0.0)
+    rng = np.random.default_rng(seed)
+    flagged = 0
+    for t in range(steps):
+        st = env.state_arrays()
+        s = to_oracle_state(o, st)
+        act_t = None
+        act_o = None
+        if actions:
+            a = rng.uniform(-0.3, 0.3, (env.total_robots, 2)).astype(env.np_dtype)
+            act_t = torch.from_numpy(a).cuda()
+            act_o = a.astype(np.float64)
+        obs_o, rew_o, done_o, tr = oracle.step(o, seed, s, actions=act_o, trace=True)
+        env.step(actions=act_t, **b)
+        torch.cuda.synchronize()
+        st2 = env.state_arrays()
+        done_g = b["done"].cpu().numpy()
+        assert np.array_equal(done_g, done_o), f"done differs at step {t}"
+        err["u_nom"] = max(err["u_nom"], np.abs(b["u_nom"].cpu().numpy() - tr["u_nom"]).max())
+        err["u_star"] = max(err["u_star"], np.abs(b["u_star"].cpu().numpy() - tr["u_star"]).max())
+        vw = b["vw"].cpu().numpy()
+        err["v"] = max(err["v"], np.abs(vw[:, 0] - tr["vw"][:, 0]).max())
+        err["w"] = max(err["w"], np.abs(vw[:, 1] - tr["vw"][:, 1]).max())
+        err["pose"] = max(err["pose"], np.abs(st2["x"] - s.x).max(), np.abs(st2["y"] - s.y).max())
+        err["th"] = max(err["th"], np.abs(wrap(st2["th"] - s.th)).max())
+        err["rew"] = max(err["rew"], np.abs(b["reward"].cpu().numpy() - rew_o).max())
+        err["obs"] = max(err["obs"], obs_diff(b["obs"].cpu().numpy(), obs_o, g["scenario"],
+                                              g["n_max"], g["r_max"]))
+        assert np.array_equal(st2["t"], s.t) and np.array_equal(st2["ep"], s.ep)
+        assert np.array_equal(st2["level"], s.level)
+        if o["r_max"] > 0:
+            assert np.array_equal(st2["qactive"], s.qactive), f"resources differ at step {t}"
+        cg, co = st2["counters"], s.counters.reshape(-1, 8)
+        for c in (0, 1, 2, 6):
+            assert np.array_equal(cg[:, c], co[:, c]), f"counter {c} differs at step {t}"
+        qi = b["qp_info"].cpu().numpy()
+        flagged += int(((qi[:, 3] >> 1) & 1).sum())
+    env.close()
+    return err, flagged
+
+
+@pytest.mark.parametrize("case", ["nav4_scripted", "nav4_policy", "nav10", "forage_uneven",
+                                  "nav20_near"])
+def test_teacher_forced_binary32(rl, case):
+    seed = 77
+    if case == "nav4_scripted":
+        g, o = make_pair(0, 4)
+        n, steps, act = [4] * 300, 40, False
+    elif case == "nav4_policy":
+        g, o = make_pair(0, 4, scripted=0)
+        n, steps, act = [4] * 300, 30, True
+    elif case == "nav10":
+        g, o = make_pair(0, 10)
+        n, steps, act = [10] * 96, 30, False
+    elif case == "forage_uneven":
+        g, o = make_pair(1, 10, episode_len=30)
+        n, steps, act = list(np.random.default_rng(2).integers(2, 11, 200)), 40, False
+    else:
+        g, o = make_pair(0, 20, near_frac=0.3)
+        n, steps, act = [20] * 40, 25, False
+    err, flagged = _teacher_forced(rl, g, o, n, seed, steps, actions=act)
+    print(f"\n{case}: max errors {err}  fp64-resolved QPs {flagged}")
+    assert err["u_nom"] < 1e-6
+    assert err["u_star"] < U_TOL
+    assert err["v"] < U_TOL and err["w"] < U_TOL / g["l"]
+    assert err["pose"] < 1e-6 and err["th"] < 1e-5
+    assert err["rew"] < 1e-5 and err["obs"] < 1e-5
+
+
+def test_teacher_forced_binary64(rl):
+    g, o = make_pair(0, 4, 64)
+    err, _ = _teacher_forced(rl, g, o, [4] * 64, 5, 30)
+    print(f"\nfp64 teacher-forced: {err}")
+    for k, v in err.items():
+        assert v < 1e-11, (k, v)
+
+
+def test_tiny_config_free_run_binary64(rl):
+    """16 envs x 4 robots, 100 steps, binary64: one full episode, ending in auto-reset."""
+    g, o = make_pair(0, 4, 64)
+    n, seed, T = [4] * 16, 0, 100
+    env = rl.Env(g, 16, n, seed)
+    b = _alloc(env, T)
+    env.rollout(T, **b)
+    torch.cuda.synchronize()
+    s = oracle.reset(o, seed, n)
+    obs_o, rew_o, done_o = oracle.rollout(o, seed, s, T)
+    d_obs = obs_diff(b["obs"].cpu().numpy(), obs_o, 0, 4, 0)
+    d_rew = np.abs(b["reward"].cpu().numpy() - rew_o).max()
+    print(f"\ntiny fp64 free run: obs {d_obs:.3e} reward {d_rew:.3e}")
+    assert np.array_equal(b["done"].cpu().numpy(), done_o)
+    assert done_o[-1].all() and not done_o[:-1].any()
+    assert d_obs < 1e-9 and d_rew < 1e-9
+    assert np.array_equal(env.counters()[:, [0, 1, 2, 6]], s.counters.reshape(-1, 8)[:, [0, 1, 2, 6]])
+    env.close()
+
+
+@pytest.mark.parametrize("N,E", [(4, 16), (4, 257), (10, 64)])
+def test_free_run_binary32_poses_after_100_steps(rl, N, E):
+    g, o = make_pair(0, N, episode_len=1000)
+    n, seed = [N] * E, 3
+    env = rl.Env(g, E, n, seed)
+    env.rollout(100)
+    st = env.state_arrays()
+    s = oracle.reset(o, seed, n)
+    oracle.rollout(o, seed, s, 100, want_obs=False)
+    dp = max(np.abs(st["x"] - s.x).max(), np.abs(st["y"] - s.y).max())
+    dth = np.abs(wrap(st["th"] - s.th)).max()
+    print(f"\nN={N} E={E} fp32 free run 100 steps: max pose err {dp:.3e} m, heading {dth:.3e}")
+    assert dp < POSE_TOL
+    env.close()
+
+
+def test_rollout_equals_steps_and_plain_form(rl):
+    g, _ = make_pair(0, 4, episode_len=20)
+    n, T = [4] * 130, 45
+    a = rl.Env(g, 130, n, 9)
+    bt = _alloc(a, T)
+    a.rollout(T, **bt)
+    b = rl.Env(g, 130, n, 9)
+    for t in range(T):
+        bs = _alloc(b)
+        b.step(obs=bs["obs"], reward=bs["reward"], done=bs["done"])
+        assert torch.equal(bs["obs"], bt["obs"][t]) and torch.equal(bs["reward"], bt["reward"][t])
+        assert torch.equal(bs["done"], bt["done"][t])
+    c = rl.Env(g, 130, n, 9)
+    bp = _alloc(c, T)
+    c.rollout(T, plain=True, **bp)
+    assert torch.equal(bp["obs"], bt["obs"]) and torch.equal(bp["done"], bt["done"])
+    assert a.get_state() == b.get_state() == c.get_state()
+    for e in (a, b, c):
+        e.close()
+
+
+def test_uneven_classes_in_one_batch(rl):
+    """Envs of 2..32 robots (every size class, ragged class sizes) in one handle."""
+    n = [2, 3, 4, 5, 7, 8, 9, 12, 16, 17, 25, 32] * 5
+    g, o = make_pair(0, 32)
+    err, _ = _teacher_forced(rl, g, o, n, 4, 12)
+    print(f"\nuneven classes: {err}")
+    assert err["u_star"] < U_TOL and err["pose"] < 1e-6
+
+
+def test_checkpoint_resume_bit_identical(rl):
+    g, _ = make_pair(1, 8)
+    n = list(np.random.default_rng(1).integers(2, 9, 100))
+    env = rl.Env(g, 100, n, 12)
+    env.rollout(37)
+    blob = env.get_state()
+    b1 = _alloc(env, 50)
+    env.rollout(50, **b1)
+    s1 = env.get_state()
+    env.set_state(blob)
+    b2 = _alloc(env, 50)
+    env.rollout(50, **b2)
+    assert env.get_state() == s1
+    assert torch.equal(b1["obs"], b2["obs"]) and torch.equal(b1["reward"], b2["reward"])
+    env.close()
+
+
+def test_rollout_host_matches_device(rl):
+    g, _ = make_pair(0, 4)
+    env = rl.Env(g, 64, 4, 21)
+    blob = env.get_state()
+    T = 30
+    b = _alloc(env, T)
+    env.rollout(T, **b)
+    ho = np.zeros((T, env.total_robots, env.obs_dim), np.float32)
+    hr = np.zeros((T, 64), np.float32)
+    hd = np.zeros((T, 64), np.uint8)
+    env.rollout_host(T, state=blob, obs=ho, reward=hr, done=hd)
+    assert np.array_equal(ho, b["obs"].cpu().numpy())
+    assert np.array_equal(hr, b["reward"].cpu().numpy())
+    env.close()
+
+
+def test_determinism_same_seed(rl):
+    g, _ = make_pair(0, 20, near_frac=0.3)
+    outs = []
+    for _ in range(2):
+        env = rl.Env(g, 50, 20, 123)
+        b = _alloc(env, 20)
+        env.rollout(20, **b)
+        outs.append((b["obs"].cpu().numpy(), env.get_state()))
+        env.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+def test_argument_errors(rl):
+    g, _ = make_pair(0, 4)
+    env = rl.Env(g, 8, 4, 0)
+    with pytest.raises(rl.RLError):
+        env.step(actions=torch.zeros(32, 2, device="cuda"))  # scripted handle takes no actions
+    with pytest.raises(rl.RLError):
+        env.set_state(b"\0" * env.state_bytes())
+    env.close()
+    with pytest.raises(rl.RLError):
+        rl.Env(dict(g, episode_len=0), 8, 4, 0)
+    with pytest.raises(rl.RLError):
+        rl.Env(g, 8, 33, 0)
