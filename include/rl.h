@@ -83,7 +83,8 @@ typedef struct {
     int32_t max_attempts;   /* rejection-sampling attempts per robot at reset */
     int32_t qp_max_iter;    /* active-set iteration cap (0: 8 * n_max + 16) */
     int32_t resolve_f64;    /* 1: re-solve flagged binary32 QPs in binary64 */
-    int32_t lanes;          /* lanes per environment (0: chosen by the library's tuner) */
+    int32_t lanes;          /* lanes per environment (0: the class default or rl_tune's pick) */
+    int32_t block_threads;  /* threads per block, a multiple of 32 up to 256 (0: default) */
     double gamma;           /* barrier gain (100) */
     double r;               /* safety radius [m] (0.17) */
     double l;               /* projection distance [m] (0.05) */

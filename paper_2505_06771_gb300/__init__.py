@@ -40,7 +40,8 @@ class RLError(RuntimeError):
 class RLConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("scenario", "precision", "scripted", "episode_len", "n_res_min", "n_res_max",
-                 "r_max", "n_max", "max_attempts", "qp_max_iter", "resolve_f64", "lanes")] + \
+                 "r_max", "n_max", "max_attempts", "qp_max_iter", "resolve_f64", "lanes",
+                 "block_threads")] + \
                [(n, ctypes.c_double) for n in
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",

@@ -1,0 +1,742 @@
+// env_small.cuh -- the step for environments of at most 4 robots (binary32), register-resident.
+//
+// Same method and same results (up to rounding) as run_env in env_step.cuh, specialised for the
+// 4-robot class: a team of 4 lanes, lane i owning robot i, pose and heading in registers for the
+// whole launch.  After the nominal velocities are formed the team all-gathers the projected
+// points and nominal velocities with warp shuffles; the barrier rows are evaluated in registers
+// (lane i takes its circulant pair rows and its four arena rows) and reduced with shuffles.
+// Most QPs end with no active row or exactly one; the dual active-set method's first iteration
+// is then the closed-form projection onto that row's half-plane, confirmed by a second scan.
+// Only when a second row is violated does the team hand the QP to the general shared-memory
+// solver.  Rare work -- the auto-reset sampler and the binary64 re-solve of a flagged QP --
+// also goes through the shared-memory code of env_step.cuh.
+#pragma once
+#include "env_step.cuh"
+
+namespace rl {
+
+template <typename T>
+__device__ __forceinline__ T pick4(const T (&a)[4], int k) {
+    T r = a[0];
+    if (k == 1) r = a[1];
+    if (k == 2) r = a[2];
+    if (k == 3) r = a[3];
+    return r;
+}
+
+constexpr int kRegRows = 4;  // active rows the register solver holds (more: shared memory)
+
+// Most violated row of the lane's own rows (circulant pair rows + its four arena rows), the q
+// active rows ak[0..q) skipped, reduced over the team: ties to the lowest row index.
+__device__ __forceinline__ void small_scan(const Team<4>& tm, int N, int P, int ndi,
+                                           const float (&Px)[4], const float (&Py)[4],
+                                           const float (&U)[8], const QPConsts<float>& c,
+                                           const int (&ak)[kRegRows], int q, float& vb, int& kb) {
+    const int i = tm.lane;
+    vb = 0.f;
+    kb = 0x7fffffff;
+    if (i < N) {
+        const float pxi = pick4(Px, i), pyi = pick4(Py, i);
+        float Ux[4], Uy[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) { Ux[m] = U[2 * m]; Uy[m] = U[2 * m + 1]; }
+        const float uxi = pick4(Ux, i), uyi = pick4(Uy, i);
+#pragma unroll
+        for (int d = 1; d <= 2; ++d) {
+            if (d <= ndi) {
+                int j = i + d;
+                if (j >= N) j -= N;
+                const int a = min(i, j), b = max(i, j);
+                const int k = pair_index(a, b, N);
+                bool act = false;
+#pragma unroll
+                for (int t = 0; t < kRegRows; ++t) act |= (t < q && ak[t] == k);
+                const float sgn = (a == i) ? 1.f : -1.f;
+                const float dx = sgn * (pxi - pick4(Px, j)), dy = sgn * (pyi - pick4(Py, j));
+                const float dux = sgn * (uxi - pick4(Ux, j)), duy = sgn * (uyi - pick4(Uy, j));
+                const float h = dx * dx + dy * dy - c.r2;
+                const float bv = c.gamma * h * h * h;
+                const float v = -2.f * (dx * dux + dy * duy) - bv;
+                if (!act && v > c.tol_abs + c.tol_rel * fabsf(bv) &&
+                    (v > vb || (v == vb && k < kb))) {
+                    vb = v;
+                    kb = k;
+                }
+            }
+        }
+        const float bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
+        const float by0 = c.ymax - c.half_r - pyi, by1 = pyi - c.ymin - c.half_r;
+        const float bvs[4] = {c.kg * bx0 * bx0 * bx0, c.kg * bx1 * bx1 * bx1,
+                              c.kg * by0 * by0 * by0, c.kg * by1 * by1 * by1};
+        const float aus[4] = {uxi, -uxi, uyi, -uyi};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int k = P + 4 * i + s;
+            bool act = false;
+#pragma unroll
+            for (int t = 0; t < kRegRows; ++t) act |= (t < q && ak[t] == k);
+            const float v = aus[s] - bvs[s];
+            if (!act && v > c.tol_abs + c.tol_rel * fabsf(bvs[s]) &&
+                (v > vb || (v == vb && k < kb))) {
+                vb = v;
+                kb = k;
+            }
+        }
+    }
+    tm.argmax(vb, kb);
+}
+
+// Row k as a dense coefficient vector over u = [u_0x, u_0y, ..., u_3x, u_3y], its bound b and,
+// for a pair row, h = |p_a - p_b|^2 - r^2 (arena rows: h = +inf).
+__device__ __forceinline__ void small_row(int k, int N, int P, const float (&Px)[4],
+                                          const float (&Py)[4], const QPConsts<float>& c,
+                                          float (&a)[8], float& b, float& h) {
+    int ia, ib;
+    float ax, ay;
+    if (k < P) {
+        int pa, pb;
+        pair_of(k, N, pa, pb);
+        const float dx = pick4(Px, pa) - pick4(Px, pb), dy = pick4(Py, pa) - pick4(Py, pb);
+        h = dx * dx + dy * dy - c.r2;
+        ia = pa;
+        ib = pb;
+        ax = -2.f * dx;
+        ay = -2.f * dy;
+        b = c.gamma * h * h * h;
+    } else {
+        const int r = k - P;
+        ia = r >> 2;
+        ib = -1;
+        const int s = r & 3;
+        const float pxi = pick4(Px, ia), pyi = pick4(Py, ia);
+        float d;
+        if (s == 0) { ax = 1.f; ay = 0.f; d = c.xmax - c.half_r - pxi; }
+        else if (s == 1) { ax = -1.f; ay = 0.f; d = pxi - c.xmin - c.half_r; }
+        else if (s == 2) { ax = 0.f; ay = 1.f; d = c.ymax - c.half_r - pyi; }
+        else { ax = 0.f; ay = -1.f; d = pyi - c.ymin - c.half_r; }
+        b = c.kg * d * d * d;
+        h = CUDART_INF_F;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        a[2 * m] = (m == ia) ? ax : ((m == ib) ? -ax : 0.f);
+        a[2 * m + 1] = (m == ia) ? ay : ((m == ib) ? -ay : 0.f);
+    }
+}
+
+__device__ __forceinline__ float dot8(const float (&a)[8], const float (&b)[8]) {
+    float s = 0.f;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) s += a[m] * b[m];
+    return s;
+}
+
+__device__ __forceinline__ int ltri(int i, int k) { return i * (i + 1) / 2 + k; }
+
+// General shared-memory solver for the QPs whose active set outgrows the register solver (out
+// of line, so the hot loop stays small).
+__device__ __noinline__ QPResult small_general(const Team<4> tm, TeamSmem<float, 4>& S, int N,
+                                               float px, float py, float u0x, float u0y,
+                                               const QPConsts<float> c) {
+    QPWork<float, 4>& W = S.qp.f;
+    const int i = tm.lane;
+    if (i < N) {
+        W.px[i] = px;
+        W.py[i] = py;
+        W.u0x[i] = W.ux[i] = u0x;
+        W.u0y[i] = W.uy[i] = u0y;
+    }
+    tm.sync();
+    return qp_solve<float, 4, 4>(tm, W, N, c);  // the minimiser is left in W.ux / W.uy
+}
+
+// The barrier QP of one env of N <= 4 robots, filtered velocity of the lane's own robot.
+// The dual active-set method runs in registers on dense 8-vectors with up to kRegRows active
+// rows; every lane of the team computes the same iterates.  The common cases cost one scan (no
+// active row) or one closed-form half-plane projection and a confirming scan (one active row).
+// An active set larger than kRegRows goes to the shared-memory solver.
+__device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<float, 4>& S, int N,
+                                                 const float (&Px)[4], const float (&Py)[4],
+                                                 const float (&U0x)[4], const float (&U0y)[4],
+                                                 const QPConsts<float>& c, float& usx,
+                                                 float& usy) {
+    QPResult res;
+    res.status = 0;
+    res.q = 0;
+    res.iters = 0;
+    res.flag = false;
+    const int i = tm.lane;
+    const int P = N * (N - 1) / 2;
+    const int nd = (N - 1) / 2;
+    const int ndi = (i < N) ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
+    float U[8];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        U[2 * m] = U0x[m];
+        U[2 * m + 1] = U0y[m];
+    }
+    int ak[kRegRows];
+    float AR[kRegRows][8], lam[kRegRows], ah[kRegRows];
+    float L[kRegRows * (kRegRows + 1) / 2], dinv[kRegRows];
+#pragma unroll
+    for (int t = 0; t < kRegRows; ++t) ak[t] = -1;
+    int q = 0;
+    float vb;
+    int kb;
+    small_scan(tm, N, P, ndi, Px, Py, U, c, ak, 0, vb, kb);
+    if (kb != 0x7fffffff) {
+        // first iteration in closed form: the projection onto the half-plane of row kb
+        float ap[8], bp, hp;
+        small_row(kb, N, P, Px, Py, c, ap, bp, hp);
+        const float app = dot8(ap, ap);
+        const float st = (dot8(ap, U) - bp) / app;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            U[m] -= st * ap[m];
+            AR[0][m] = ap[m];
+        }
+        const float dg = sqrtf(app);
+        L[0] = dg;
+        dinv[0] = 1.f / dg;
+        ak[0] = kb;
+        lam[0] = st;
+        ah[0] = hp;
+        q = 1;
+        res.iters = 1;
+        small_scan(tm, N, P, ndi, Px, Py, U, c, ak, 1, vb, kb);
+    }
+    bool overflow = false;
+    while (kb != 0x7fffffff) {
+        if (++res.iters > c.max_iter) { res.status = 2; break; }
+        float ap[8], bp, hp;
+        small_row(kb, N, P, Px, Py, c, ap, bp, hp);
+        const float app = dot8(ap, ap);
+        float lam_p = 0.f;
+        bool added = false;
+        for (int guard = 0; guard <= kRegRows + 1 && !added; ++guard) {
+            // r = G^-1 N^T a_p (forward and back substitution), z = a_p - N r
+            float y[kRegRows], r[kRegRows];
+#pragma unroll
+            for (int t = 0; t < kRegRows; ++t) {
+                y[t] = 0.f;
+                if (t < q) {
+                    float s = dot8(AR[t], ap);
+#pragma unroll
+                    for (int m = 0; m < t; ++m) s -= L[ltri(t, m)] * y[m];
+                    y[t] = s * dinv[t];
+                }
+            }
+#pragma unroll
+            for (int t = kRegRows - 1; t >= 0; --t) {
+                r[t] = 0.f;
+                if (t < q) {
+                    float s = y[t];
+#pragma unroll
+                    for (int m = t + 1; m < kRegRows; ++m)
+                        if (m < q) s -= L[ltri(m, t)] * r[m];
+                    r[t] = s * dinv[t];
+                }
+            }
+            float z[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) z[m] = ap[m];
+#pragma unroll
+            for (int t = 0; t < kRegRows; ++t)
+                if (t < q) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) z[m] -= r[t] * AR[t][m];
+                }
+            const float zz = dot8(z, z);
+            float td = CUDART_INF_F;
+            int jb = -1;
+#pragma unroll
+            for (int t = 0; t < kRegRows; ++t)
+                if (t < q && r[t] > 0.f) {
+                    const float tj = lam[t] / r[t];
+                    if (tj < td) { td = tj; jb = t; }
+                }
+            const float sp = dot8(ap, U) - bp;
+            const bool indep = zz > c.eps_dep * app;
+            if (!indep) res.flag = true;
+            const float tf = indep ? sp / zz : CUDART_INF_F;
+            if (!(tf < CUDART_INF_F) && !(td < CUDART_INF_F)) {
+                res.status = 1;
+                break;
+            }
+            const float st = tf < td ? tf : td;
+            if (tf < CUDART_INF_F) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) U[m] -= st * z[m];
+            }
+#pragma unroll
+            for (int t = 0; t < kRegRows; ++t)
+                if (t < q) lam[t] -= st * r[t];
+            lam_p += st;
+            if (tf <= td) {
+                if (q == kRegRows) { overflow = true; break; }
+                const float dg = sqrtf(zz);
+#pragma unroll
+                for (int t = 0; t < kRegRows; ++t) {
+                    if (t == q) {
+#pragma unroll
+                        for (int m = 0; m < t; ++m) L[ltri(t, m)] = y[m];
+                        L[ltri(t, t)] = dg;
+                        dinv[t] = 1.f / dg;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) AR[t][m] = ap[m];
+                        ak[t] = kb;
+                        lam[t] = lam_p;
+                        ah[t] = hp;
+                    }
+                }
+                ++q;
+                added = true;
+            } else {
+                // drop row jb and refactor the Gram matrix of the remaining rows
+#pragma unroll
+                for (int t = 0; t < kRegRows - 1; ++t)
+                    if (t >= jb) {
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) AR[t][m] = AR[t + 1][m];
+                        ak[t] = ak[t + 1];
+                        lam[t] = lam[t + 1];
+                        ah[t] = ah[t + 1];
+                    }
+                --q;
+                ak[q] = -1;
+                bool ok = true;
+#pragma unroll
+                for (int t = 0; t < kRegRows; ++t)
+                    if (t < q) {
+#pragma unroll
+                        for (int m = 0; m <= t; ++m) {
+                            float g = dot8(AR[t], AR[m]);
+#pragma unroll
+                            for (int n = 0; n < m; ++n) g -= L[ltri(t, n)] * L[ltri(m, n)];
+                            if (m == t) {
+                                ok = ok && (g > 0.f);
+                                const float dg = sqrtf(fmaxf(g, 1e-30f));
+                                L[ltri(t, t)] = dg;
+                                dinv[t] = 1.f / dg;
+                            } else {
+                                L[ltri(t, m)] = g * dinv[m];
+                            }
+                        }
+                    }
+                if (!ok) { res.status = 2; break; }
+            }
+        }
+        if (res.status != 0 || overflow) break;
+        if (!added) { res.status = 2; break; }
+        small_scan(tm, N, P, ndi, Px, Py, U, c, ak, q, vb, kb);
+    }
+    if (overflow) {
+        res = small_general(tm, S, N, pick4(Px, i), pick4(Py, i), pick4(U0x, i), pick4(U0y, i), c);
+        usx = (i < N) ? S.qp.f.ux[i] : 0.f;
+        usy = (i < N) ? S.qp.f.uy[i] : 0.f;
+        tm.sync();
+        return res;
+    }
+    res.q = q;
+    if (res.status == 0) {
+#pragma unroll
+        for (int t = 0; t < kRegRows; ++t)
+            if (t < q && ah[t] < c.h_flag) res.flag = true;  // near-degenerate pair row
+    } else {
+        res.flag = true;
+        if (res.status == 1) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) U[m] = 0.f;
+        }
+    }
+    float Ux[4], Uy[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) { Ux[m] = U[2 * m]; Uy[m] = U[2 * m + 1]; }
+    usx = pick4(Ux, i);
+    usy = pick4(Uy, i);
+    return res;
+}
+
+// binary64 re-solve of a flagged QP by the team, through the shared-memory solver.
+__device__ __noinline__ QPResult small_resolve_f64(const Team<4> tm, TeamSmem<float, 4>& S,
+                                                   const StepConsts<float> k, int N, float x,
+                                                   float y, float th, float u0x, float u0y) {
+    QPWork<double, 4>& D = S.qp.d;
+    QPConsts<double> dc;
+    dc.gamma = (double)k.gamma; dc.r2 = (double)k.r2; dc.kg = (double)k.kg;
+    dc.half_r = (double)k.half_r; dc.xmin = (double)k.xmin; dc.xmax = (double)k.xmax;
+    dc.ymin = (double)k.ymin; dc.ymax = (double)k.ymax; dc.h_flag = (double)k.h_flag;
+    dc.max_iter = 8 * 4 + 16;
+    dc.tol_abs = 1e-12; dc.tol_rel = 1e-12; dc.eps_dep = 1e-12; dc.tol_lam = 1e-10;
+    const int i = tm.lane;
+    if (i < N) {
+        double sd, cd;
+        sincos((double)th, &sd, &cd);
+        D.px[i] = (double)x + (double)k.l * cd;
+        D.py[i] = (double)y + (double)k.l * sd;
+        D.u0x[i] = (double)u0x;
+        D.u0y[i] = (double)u0y;
+        D.ux[i] = D.u0x[i];
+        D.uy[i] = D.u0y[i];
+    }
+    tm.sync();
+    return qp_solve<double, 4, 4>(tm, D, N, dc);  // the minimiser is left in D.ux / D.uy
+}
+
+// Auto-reset: samples episode ep into S.fx/fy/fth (poses), S.sx/sy (goals), S.slevel (levels)
+// and the resources; returns the resource count.
+__device__ __noinline__ int small_reset(const Team<4> tm, TeamSmem<float, 4>& S,
+                                        const LaunchArgs<float> A, int e, int ep, int N) {
+    int n_res = 0;
+    team_sample<float, 4, 4>(tm, S, A, e, ep, N, n_res);
+    const int i = tm.lane;
+    if (i < N) {
+        float gx, gy;
+        int lv;
+        robot_goal_level<float>(A, e, ep, i, gx, gy, lv);
+        S.sx[i] = gx;
+        S.sy[i] = gy;
+        S.slevel[i] = lv;
+    }
+    tm.sync();
+    return n_res;
+}
+
+__device__ __forceinline__ float wrap_pi_f(float a) {
+    a = (a > CUDART_PI_F) ? a - 2.f * CUDART_PI_F : a;
+    return (a <= -CUDART_PI_F) ? a + 2.f * CUDART_PI_F : a;
+}
+
+// |(a, b)| through the reciprocal square root (relative error a few 1e-7).
+__device__ __forceinline__ float fast_norm(float a, float b) {
+    const float n2 = a * a + b * b;
+    return n2 > 0.f ? n2 * rsqrtf(n2) : 0.f;
+}
+
+// |u| <= m by scaling, without a branch: s = min(1, m / |u|).
+__device__ __forceinline__ void cap_fast(float& ux, float& uy, float m) {
+    const float s = fminf(1.f, m * rsqrtf(ux * ux + uy * uy));
+    ux *= s;
+    uy *= s;
+}
+
+// Out-of-line rare paths of the foraging scenario.
+__device__ __noinline__ void small_forage_target(const TeamSmem<float, 4>& S, int n_res, float px,
+                                                 float py, float& tx, float& ty) {
+    int best = -1;
+    float bd = 0.f;
+    for (int r = 0; r < n_res; ++r) {
+        if (!S.qactive[r]) continue;
+        const float dx = S.qx[r] - px, dy = S.qy[r] - py;
+        const float d2 = dx * dx + dy * dy;
+        if (best < 0 || d2 < bd) { best = r; bd = d2; }
+    }
+    if (best >= 0) { tx = S.qx[best]; ty = S.qy[best]; }
+    else { tx = px; ty = py; }
+}
+
+__device__ __noinline__ void small_forage_obs(const TeamSmem<float, 4>& S, const StepConsts<float> k,
+                                              float* o, int i, int N, int n_res, float x, float y,
+                                              float th, int lv, const float (&X)[4],
+                                              const float (&Y)[4], const float (&TH)[4],
+                                              const int (&LV)[4]) {
+    o[0] = x; o[1] = y; o[2] = th; o[3] = (float)lv;
+    int c = 4;
+    for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        o[c] = pick4(X, j) - x;
+        o[c + 1] = pick4(Y, j) - y;
+        o[c + 2] = wrap_pi_f(pick4(TH, j) - th);
+        o[c + 3] = (float)pick4(LV, j);
+        c += 4;
+    }
+    const int rbase = 4 + 4 * (k.n_max_obs - 1);
+    for (; c < rbase; ++c) o[c] = 0.f;
+    for (int r = 0; r < k.r_max; ++r) {
+        if (r < n_res) {
+            o[c] = S.qx[r] - x;
+            o[c + 1] = S.qy[r] - y;
+            o[c + 2] = (float)S.qlevel[r];
+            o[c + 3] = (float)S.qactive[r];
+        } else {
+            o[c] = o[c + 1] = o[c + 2] = o[c + 3] = 0.f;
+        }
+        c += 4;
+    }
+}
+
+// One env of at most 4 robots for T steps (team of 4 lanes).  FAST: the Navigation scenario with
+// scripted nominal control and no traces, every such branch folded away at compile time.
+template <bool FAST>
+__device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
+                              TeamSmem<float, 4>& S, int e) {
+    const StepConsts<float>& k = A.k;
+    const int off = A.s.off[e];
+    const int N = A.s.nrob[e];
+    const bool forage = !FAST && (k.scenario == 1);
+    const float* actions = FAST ? nullptr : A.io.actions;
+    float* tr_unom = FAST ? nullptr : A.io.u_nom;
+    float* tr_ustar = FAST ? nullptr : A.io.u_star;
+    float* tr_vw = FAST ? nullptr : A.io.vw;
+    int32_t* tr_qp = FAST ? nullptr : A.io.qp_info;
+    const int i = tm.lane;
+    const bool own = i < N;
+    const int row = off + (own ? i : 0);
+
+    QPConsts<float> qc;
+    qc.gamma = k.gamma; qc.r2 = k.r2; qc.kg = k.kg; qc.half_r = k.half_r;
+    qc.xmin = k.xmin; qc.xmax = k.xmax; qc.ymin = k.ymin; qc.ymax = k.ymax;
+    qc.h_flag = k.h_flag;
+    qc.max_iter = k.max_iter;
+    qc.tol_abs = 2e-7f; qc.tol_rel = 1e-6f; qc.eps_dep = 1e-5f; qc.tol_lam = 1e-6f;
+
+    float x = A.s.x[row], y = A.s.y[row], th = A.s.th[row];
+    float gx = A.s.gx[row], gy = A.s.gy[row];
+    int lv = A.s.level[row];
+    float sn, cs;
+    __sincosf(th, &sn, &cs);
+    int t = A.s.t[e], ep = A.s.ep[e];
+    int n_res = 0;
+    if (forage) {
+        n_res = A.s.n_res[e];
+        for (int r = i; r < k.r_max; r += 4) {
+            S.qx[r] = A.s.qx[e * k.r_max + r];
+            S.qy[r] = A.s.qy[e * k.r_max + r];
+            S.qlevel[r] = A.s.qlevel[e * k.r_max + r];
+            S.qactive[r] = A.s.qactive[e * k.r_max + r];
+        }
+    }
+    // counters, kept by lane 0
+    int c_col = 0, c_oob = 0, c_succ = 0, c_act = 0, c_flag = 0, c_inf = 0, c_ep = 0, c_it = 0;
+    tm.sync();
+    const int nd = (N - 1) / 2;
+    const int ndi = own ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
+    const float* acts = actions;
+
+    for (int step = 0; step < A.T; ++step) {
+        // ---- projected point and nominal SI velocity of the own robot
+        const float px = x + k.l * cs, py = y + k.l * sn;
+        float ux, uy;
+        if (!FAST && acts) {
+            ux = acts[2 * row];
+            uy = acts[2 * row + 1];
+        } else {
+            float tx = gx, ty = gy;
+            if (forage) small_forage_target(S, n_res, px, py, tx, ty);
+            ux = k.k_si * (tx - px);
+            uy = k.k_si * (ty - py);
+            cap_fast(ux, uy, k.vmax);
+            const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)t);
+            const uint32_t wx = (i & 1) ? w.w[2] : w.w[0], wy = (i & 1) ? w.w[3] : w.w[1];
+            const float ex = __fmul_rn(__fsub_rn(unit24(wx), 0.5f), k.noise_scale);
+            const float ey = __fmul_rn(__fsub_rn(unit24(wy), 0.5f), k.noise_scale);
+            ux += k.noise_on ? ex : 0.f;
+            uy += k.noise_on ? ey : 0.f;
+        }
+        cap_fast(ux, uy, k.vmax);
+        const float dold = fast_norm(px - gx, py - gy);
+        // ---- all-gather and the barrier QP
+        float Px[4], Py[4], U0x[4], U0y[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            Px[r] = __shfl_sync(tm.mask, px, r, 4);
+            Py[r] = __shfl_sync(tm.mask, py, r, 4);
+            U0x[r] = __shfl_sync(tm.mask, ux, r, 4);
+            U0y[r] = __shfl_sync(tm.mask, uy, r, 4);
+        }
+        float usx, usy;
+        QPResult res = small_filter(tm, S, N, Px, Py, U0x, U0y, qc, usx, usy);
+        int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
+        if (k.resolve_f64 && res.flag) {
+            const QPResult r64 = small_resolve_f64(tm, S, k, N, x, y, th, ux, uy);
+            res.status = r64.status;
+            res.q = r64.q;
+            res.iters += r64.iters;
+            usx = own ? (float)S.qp.d.ux[i] : 0.f;
+            usy = own ? (float)S.qp.d.uy[i] : 0.f;
+            tm.sync();
+            qflags |= 2;
+        }
+        // ---- SI -> unicycle, wheel clip, Euler step
+        float v = cs * usx + sn * usy;
+        float om = (cs * usy - sn * usx) * k.inv_l;
+        const float wr = fminf(fmaxf(v + k.half_track * om, -k.vmax), k.vmax);
+        const float wl = fminf(fmaxf(v - k.half_track * om, -k.vmax), k.vmax);
+        v = 0.5f * (wr + wl);
+        om = (wr - wl) * k.inv_track;
+        if (!FAST && own) {
+            if (tr_unom) { tr_unom[2 * row] = ux; tr_unom[2 * row + 1] = uy; }
+            if (tr_ustar) { tr_ustar[2 * row] = usx; tr_ustar[2 * row + 1] = usy; }
+            if (tr_vw) { tr_vw[2 * row] = v; tr_vw[2 * row + 1] = om; }
+        }
+        x += k.dt * v * cs;
+        y += k.dt * v * sn;
+        th = wrap_pi_f(th + k.dt * om);
+        __sincosf(th, &sn, &cs);
+        const float npx = x + k.l * cs, npy = y + k.l * sn;
+        // ---- flags, reward, scenario transition
+        float Qx[4], Qy[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            Qx[r] = __shfl_sync(tm.mask, npx, r, 4);
+            Qy[r] = __shfl_sync(tm.mask, npy, r, 4);
+        }
+        int flags_l = 0;  // collisions in the low half, out-of-arena in the high half
+#pragma unroll
+        for (int d = 1; d <= 2; ++d) {
+            int j = i + d;
+            j = (j >= N) ? j - N : j;
+            const float dx = npx - pick4(Qx, j), dy = npy - pick4(Qy, j);
+            flags_l += (d <= ndi && dx * dx + dy * dy < k.r2) ? 1 : 0;
+        }
+        flags_l += (own && (npx < k.xmin || npx > k.xmax || npy < k.ymin || npy > k.ymax)) ? 65536 : 0;
+        float rew_l = (!forage && own) ? dold - fast_norm(npx - gx, npy - gy) : 0.f;
+        const int flags = tm.sum(flags_l);
+        float rew = tm.sum(rew_l);
+        const int col = flags & 0xffff, oob = flags >> 16;
+        bool all_foraged = false;
+        int succ = 0;
+        if (forage) {
+            int remaining = 0;
+            for (int r = 0; r < n_res; ++r) {
+                if (!S.qactive[r]) continue;
+                int ls = 0;
+                if (own) {
+                    const float dx = npx - S.qx[r], dy = npy - S.qy[r];
+                    if (dx * dx + dy * dy < k.rho2) ls = lv;
+                }
+                ls = tm.sum(ls);
+                if (ls >= S.qlevel[r]) {
+                    rew += (float)S.qlevel[r];
+                    ++succ;
+                    tm.sync();
+                    if (i == 0) S.qactive[r] = 0;
+                    tm.sync();
+                } else {
+                    ++remaining;
+                }
+            }
+            all_foraged = (n_res > 0 && remaining == 0);
+        }
+        rew -= k.c_col * (float)col;
+        c_col += col;
+        c_oob += oob;
+        c_succ += succ;
+        c_act += qflags & 1;
+        c_flag += (qflags >> 1) & 1;
+        c_inf += (res.status == 1) ? 1 : 0;
+        c_it += res.iters;
+        if (!FAST && tr_qp && i == 0) {
+            tr_qp[4 * e + 0] = res.status;
+            tr_qp[4 * e + 1] = res.q;
+            tr_qp[4 * e + 2] = res.iters;
+            tr_qp[4 * e + 3] = qflags;
+        }
+        // ---- episode end and auto-reset
+        t += 1;
+        const bool done = (t >= k.episode_len) || all_foraged;
+        if (done) {
+            c_ep += 1;
+            ep += 1;
+            t = 0;
+            n_res = small_reset(tm, S, A, e, ep, N);
+            if (own) {
+                x = S.fx[i]; y = S.fy[i]; th = S.fth[i];
+                gx = S.sx[i]; gy = S.sy[i]; lv = S.slevel[i];
+            }
+            tm.sync();
+            __sincosf(th, &sn, &cs);
+        }
+        // ---- observations of the own robot
+        if (A.io.obs) {
+            float X[4], Y[4], TH[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                X[r] = __shfl_sync(tm.mask, x, r, 4);
+                Y[r] = __shfl_sync(tm.mask, y, r, 4);
+                TH[r] = __shfl_sync(tm.mask, th, r, 4);
+            }
+            const int od = A.io.obs_dim;
+            float* o = A.io.obs + (long long)step * A.io.obs_step + (long long)row * od;
+            if (!forage) {
+                // others in index order: slot s holds robot s + (s >= i)
+                float rel[9];
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl) {
+                    const int j = sl + (sl >= i ? 1 : 0);
+                    const bool live = j < N;
+                    rel[3 * sl] = live ? pick4(X, j) - x : 0.f;
+                    rel[3 * sl + 1] = live ? pick4(Y, j) - y : 0.f;
+                    rel[3 * sl + 2] = live ? wrap_pi_f(pick4(TH, j) - th) : 0.f;
+                }
+                if (own) {
+                    if (od == 14) {
+                        float2* o2 = reinterpret_cast<float2*>(o);
+                        o2[0] = make_float2(x, y);
+                        o2[1] = make_float2(th, gx);
+                        o2[2] = make_float2(gy, rel[0]);
+                        o2[3] = make_float2(rel[1], rel[2]);
+                        o2[4] = make_float2(rel[3], rel[4]);
+                        o2[5] = make_float2(rel[5], rel[6]);
+                        o2[6] = make_float2(rel[7], rel[8]);
+                    } else {
+                        const float head[5] = {x, y, th, gx, gy};
+#pragma unroll
+                        for (int s2 = 0; s2 < 5; ++s2)
+                            if (s2 < od) o[s2] = head[s2];
+#pragma unroll
+                        for (int s2 = 0; s2 < 9; ++s2)
+                            if (5 + s2 < od) o[5 + s2] = rel[s2];
+                        for (int s2 = 14; s2 < od; ++s2) o[s2] = 0.f;
+                    }
+                }
+            } else {
+                int LV[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) LV[r] = __shfl_sync(tm.mask, lv, r, 4);
+                if (own) small_forage_obs(S, k, o, i, N, n_res, x, y, th, lv, X, Y, TH, LV);
+            }
+        }
+        if (i == 0) {
+            if (A.io.reward) A.io.reward[(long long)step * A.io.E + e] = rew;
+            if (A.io.done) A.io.done[(long long)step * A.io.E + e] = done ? 1 : 0;
+        }
+    }
+    if (own) {
+        A.s.x[row] = x; A.s.y[row] = y; A.s.th[row] = th;
+        A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.level[row] = lv;
+    }
+    if (forage) {
+        tm.sync();
+        for (int r = i; r < k.r_max; r += 4) {
+            A.s.qx[e * k.r_max + r] = S.qx[r];
+            A.s.qy[e * k.r_max + r] = S.qy[r];
+            A.s.qlevel[e * k.r_max + r] = S.qlevel[r];
+            A.s.qactive[e * k.r_max + r] = S.qactive[r];
+        }
+    }
+    if (i == 0) {
+        A.s.t[e] = t;
+        A.s.ep[e] = ep;
+        if (forage) A.s.n_res[e] = n_res;
+        int32_t* cn = A.s.counters + e * kNCount;
+        cn[0] += c_col; cn[1] += c_oob; cn[2] += c_succ; cn[3] += c_act;
+        cn[4] += c_flag; cn[5] += c_inf; cn[6] += c_ep; cn[7] += c_it;
+    }
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(128, 1) env_kernel_small(LaunchArgs<float> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Team<4> tm;
+    const int teams_per_block = blockDim.x / 4;
+    const int tib = threadIdx.x / 4;
+    TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + tib;
+    const int total_teams = gridDim.x * teams_per_block;
+    for (int idx = blockIdx.x * teams_per_block + tib; idx < A.n_list; idx += total_teams) {
+        const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
+        run_env_small<FAST>(A, tm, *S, e);
+    }
+}
+
+}  // namespace rl

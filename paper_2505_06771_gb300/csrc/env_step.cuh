@@ -500,8 +500,9 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
     }
     res.q = q;
 
-    if (res.status == 0 && q > 0) {
-        // exact solve on the final active set: G lam = N^T u0 - b_A, u = u0 - N lam
+    if (std::is_same<Q, double>::value && res.status == 0 && q > 0) {
+        // binary64: exact solve on the final active set, G lam = N^T u0 - b_A, u = u0 - N lam
+        // (in binary32 the active-set iterate is already as accurate as this re-solve)
         for (int j = tm.lane; j < q; j += G) {
             Q au0;
             if (W.rib[j] >= 0)
@@ -560,7 +561,9 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
                 }
             }
         }
-        // binary32: an active pair with h below h_flag marks the QP near-degenerate
+    }
+    if (res.status == 0 && q > 0) {
+        // an active pair with h below h_flag marks the QP near-degenerate
         bool small_h = false;
         for (int j = tm.lane; j < q; j += G) {
             if (W.rib[j] >= 0) {

@@ -29,8 +29,12 @@ cudaError_t launch_one(const LaunchArgs<R>& a, int block_threads, int max_blocks
                        cudaStream_t st, bool reset) {
     if (block_threads < G || block_threads % 32 != 0 || block_threads > 256)
         return cudaErrorInvalidValue;
+    // fewer teams per block when their shared memory would exceed the 227 KB per-block limit
+    while (block_threads > 32 && (size_t)(block_threads / G) * sizeof(TeamSmem<R, NMAX>) > 227 * 1024)
+        block_threads -= 32;
     const int tpb = block_threads / G;
     const size_t smem = (size_t)tpb * sizeof(TeamSmem<R, NMAX>);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     void (*kern)(LaunchArgs<R>) = reset ? reset_kernel<R, G, NMAX> : env_kernel<R, G, NMAX>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

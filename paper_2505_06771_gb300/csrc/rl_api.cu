@@ -228,6 +228,7 @@ rl_status rl_config_default(int32_t scenario, rl_config* out) {
     out->qp_max_iter = 0;
     out->resolve_f64 = 1;
     out->lanes = 0;
+    out->block_threads = 0;
     out->gamma = 100.0;
     out->r = 0.17;
     out->l = 0.05;
@@ -324,6 +325,10 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         if (!(lanes > 0 && (ok & (unsigned)lanes))) lanes = nm;
         k.lanes = lanes;
         k.block_threads = nm <= 8 ? 64 : (nm == 16 ? 64 : 32);
+        if (cfg->block_threads > 0) {
+            if (cfg->block_threads % 32 != 0 || cfg->block_threads > 256) { rl_destroy(h); return RL_ERR_ARG; }
+            k.block_threads = std::max(cfg->block_threads, lanes);
+        }
         h->cls[h->ncls++] = k;
     }
     cudaError_t ce = cudaMalloc((void**)&h->d_lists, lists.size() * sizeof(int32_t));
