@@ -169,6 +169,29 @@ rl_status rl_get_counters(rl_env* env, int32_t* h_dst);
 /* Wait for the handle's stream; returns RL_ERR_CUDA if the device reported an error. */
 rl_status rl_sync(rl_env* env);
 
+/* Allocation-free reset + rollout.  The paper has no counterpart: this is a service for callers
+   that cannot allocate device memory -- code running while another component owns the device
+   allocator (a caching allocator that must see every allocation, a framework enforcing a fixed
+   memory budget), or code that must avoid the synchronisation a cudaMalloc/cudaFree can imply.
+   It resets n_envs envs of n_robots robots each (episode 0, seed) and runs T scripted steps,
+   with the same kernels and results as rl_create + rl_rollout on a fresh handle; the caller
+   passes the trajectory buffers (layout of rl_rollout, any may be NULL) and a stream (NULL: the
+   legacy default stream).  The environment state lives in one file-scope device array of
+   RL_NOALLOC_MAX_BYTES (8 MiB) that every GPU loading the library holds until the process
+   exits; rl_noalloc_state_bytes() gives a batch's need, and a batch that needs more returns
+   RL_ERR_ARG before any GPU work.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
+   library call.  The first call on a device looks the array's device address up
+   (cudaGetSymbolAddress) with that device current and caches it, so make that first call before
+   any stream capture.  Every call reuses the same array and overwrites what it reads (the
+   previous call's contents never leak into a result), so calls that overlap on the GPU --
+   concurrent streams, other threads, or a capture replayed while another call runs -- race.
+   Returns after enqueueing; RL_ERR_CUDA if a launch failed. */
+#define RL_NOALLOC_MAX_BYTES ((size_t)8 << 20)
+rl_status rl_rollout_noalloc(const rl_config* cfg, int32_t n_envs, int32_t n_robots,
+                             uint64_t seed, int32_t T, void* d_obs_traj, void* d_rew_traj,
+                             uint8_t* d_done_traj, void* stream);
+size_t    rl_noalloc_state_bytes(const rl_config* cfg, int32_t n_envs, int32_t n_robots);
+
 int32_t     rl_obs_dim(const rl_env* env);
 int32_t     rl_n_envs(const rl_env* env);
 int32_t     rl_total_robots(const rl_env* env);

@@ -99,6 +99,10 @@ def lib():
         L.rl_last_error.restype = ctypes.c_char_p
         L.rl_destroy.argtypes = [vp]
         L.rl_destroy.restype = None
+        L.rl_rollout_noalloc.argtypes = [ctypes.POINTER(RLConfig), i32, i32, u64, i32, vp, vp, vp,
+                                         vp]
+        L.rl_noalloc_state_bytes.argtypes = [ctypes.POINTER(RLConfig), i32, i32]
+        L.rl_noalloc_state_bytes.restype = sz
         _LIB = L
         return L
 
@@ -266,6 +270,32 @@ class Env:
     def state_arrays(self, blob: bytes | None = None) -> dict:
         """Parse a state blob (header + image of 256-byte-aligned segments) into arrays."""
         return parse_state(blob if blob is not None else self.get_state())
+
+
+def rollout_noalloc(cfg: dict, n_envs: int, n_robots: int, seed: int, T: int, obs=None,
+                    reward=None, done=None, stream=None):
+    """rl_rollout_noalloc: reset + T scripted steps with the state in the library's static
+    device array (no allocation).  Buffers as for Env.rollout; stream: a torch stream or None
+    for the current one."""
+    import torch
+    L = lib()
+    dt = torch.float64 if cfg["precision"] == 64 else torch.float32
+    rows = n_envs * n_robots
+    n_max = cfg["n_max"] if cfg["n_max"] > 0 else n_robots
+    od = (4 + 4 * (n_max - 1) + 4 * cfg["r_max"]) if cfg["scenario"] == FORAGING \
+        else 5 + 3 * (n_max - 1)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = L.rl_rollout_noalloc(ctypes.byref(_to_struct(cfg)), n_envs, n_robots, seed, T,
+                              _dptr(obs, dt, T * rows * od, "obs"),
+                              _dptr(reward, dt, T * n_envs, "reward"),
+                              _dptr(done, torch.uint8, T * n_envs, "done"),
+                              ctypes.c_void_p(s.cuda_stream))
+    if st:
+        raise RLError(st, "rl_rollout_noalloc")
+
+
+def noalloc_state_bytes(cfg: dict, n_envs: int, n_robots: int) -> int:
+    return int(lib().rl_noalloc_state_bytes(ctypes.byref(_to_struct(cfg)), n_envs, n_robots))
 
 
 _SEGS = [("x", "r", "T"), ("y", "r", "T"), ("th", "r", "T"), ("gx", "r", "T"), ("gy", "r", "T"),

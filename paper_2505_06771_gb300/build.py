@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librobo_gb300.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["rl_api.cu", "kernels_f32_small.cu", "kernels_f32_large.cu", "kernels_f64.cu"]
+SOURCES = ["rl_api.cu", "kernels_f32_small.cu", "kernels_f32_large.cu", "kernels_f64.cu",
+           "rl_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
