@@ -151,6 +151,14 @@ rl_status rl_rollout(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew_traj,
 rl_status rl_rollout_plain(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew_traj,
                            uint8_t* d_done_traj);
 
+/* Autotuner: times T_probe-step rollouts of the handle's own batch (from a saved copy of its
+   state, restored afterwards) for every launch shape -- lanes per environment and threads per
+   block for each robot-count class, and for an uneven batch one persistent launch over all
+   classes against one launch per class -- and keeps the fastest for later rollouts.
+   h_choice (NULL or 13 ints): [one-launch flag, then per class (nmax, lanes, block threads)].
+   Synchronises the stream.  RL_ERR_STATE if the handle is not scripted. */
+rl_status rl_tune(rl_env* env, int32_t T_probe, int32_t* h_choice);
+
 /* End to end through host memory: upload h_state (rl_state_bytes() bytes, or NULL to keep the
    device state), run rl_rollout, and copy the trajectories to the host buffers (pinned memory
    recommended; any may be NULL).  Returns after the copies completed. */

@@ -99,6 +99,7 @@ def lib():
         L.rl_last_error.restype = ctypes.c_char_p
         L.rl_destroy.argtypes = [vp]
         L.rl_destroy.restype = None
+        L.rl_tune.argtypes = [vp, i32, vp]
         L.rl_rollout_noalloc.argtypes = [ctypes.POINTER(RLConfig), i32, i32, u64, i32, vp, vp, vp,
                                          vp]
         L.rl_noalloc_state_bytes.argtypes = [ctypes.POINTER(RLConfig), i32, i32]
@@ -234,6 +235,16 @@ class Env:
                                             _hptr(obs, T * R * self.obs_dim, isz, "obs"),
                                             _hptr(reward, T * E, isz, "reward"),
                                             _hptr(done, T * E, 1, "done")), "rl_rollout_host")
+
+    def tune(self, T_probe: int = 50) -> dict:
+        """rl_tune: pick the fastest launch shape for this batch; returns the choice."""
+        out = np.zeros(13, np.int32)
+        self._check(self._L.rl_tune(self._h, T_probe, out.ctypes.data), "rl_tune")
+        self.lanes = int(self._L.rl_lanes(self._h))
+        return {"one_launch": bool(out[0]),
+                "classes": [dict(nmax=int(out[1 + 3 * c]), lanes=int(out[2 + 3 * c]),
+                                 block_threads=int(out[3 + 3 * c]))
+                            for c in range(4) if out[1 + 3 * c] > 0]}
 
     def state_bytes(self) -> int:
         return int(self._L.rl_state_bytes(self._h))

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librobo_gb300.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["rl_api.cu", "kernels_f32_small.cu", "kernels_f32_large.cu", "kernels_f64.cu",
-           "rl_noalloc.cu"]
+           "rl_noalloc.cu", "kernels_multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

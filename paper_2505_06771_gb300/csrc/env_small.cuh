@@ -135,7 +135,7 @@ __device__ __forceinline__ int ltri(int i, int k) { return i * (i + 1) / 2 + k; 
 
 // General shared-memory solver for the QPs whose active set outgrows the register solver (out
 // of line, so the hot loop stays small).
-__device__ __noinline__ QPResult small_general(const Team<4> tm, TeamSmem<float, 4>& S, int N,
+static __device__ __noinline__ QPResult small_general(const Team<4> tm, TeamSmem<float, 4>& S, int N,
                                                float px, float py, float u0x, float u0y,
                                                const QPConsts<float> c) {
     QPWork<float, 4>& W = S.qp.f;
@@ -358,7 +358,7 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
 }
 
 // binary64 re-solve of a flagged QP by the team, through the shared-memory solver.
-__device__ __noinline__ QPResult small_resolve_f64(const Team<4> tm, TeamSmem<float, 4>& S,
+static __device__ __noinline__ QPResult small_resolve_f64(const Team<4> tm, TeamSmem<float, 4>& S,
                                                    const StepConsts<float> k, int N, float x,
                                                    float y, float th, float u0x, float u0y) {
     QPWork<double, 4>& D = S.qp.d;
@@ -385,7 +385,7 @@ __device__ __noinline__ QPResult small_resolve_f64(const Team<4> tm, TeamSmem<fl
 
 // Auto-reset: samples episode ep into S.fx/fy/fth (poses), S.sx/sy (goals), S.slevel (levels)
 // and the resources; returns the resource count.
-__device__ __noinline__ int small_reset(const Team<4> tm, TeamSmem<float, 4>& S,
+static __device__ __noinline__ int small_reset(const Team<4> tm, TeamSmem<float, 4>& S,
                                         const LaunchArgs<float> A, int e, int ep, int N) {
     int n_res = 0;
     team_sample<float, 4, 4>(tm, S, A, e, ep, N, n_res);
@@ -421,7 +421,7 @@ __device__ __forceinline__ void cap_fast(float& ux, float& uy, float m) {
 }
 
 // Out-of-line rare paths of the foraging scenario.
-__device__ __noinline__ void small_forage_target(const TeamSmem<float, 4>& S, int n_res, float px,
+static __device__ __noinline__ void small_forage_target(const TeamSmem<float, 4>& S, int n_res, float px,
                                                  float py, float& tx, float& ty) {
     int best = -1;
     float bd = 0.f;
@@ -435,7 +435,7 @@ __device__ __noinline__ void small_forage_target(const TeamSmem<float, 4>& S, in
     else { tx = px; ty = py; }
 }
 
-__device__ __noinline__ void small_forage_obs(const TeamSmem<float, 4>& S, const StepConsts<float> k,
+static __device__ __noinline__ void small_forage_obs(const TeamSmem<float, 4>& S, const StepConsts<float> k,
                                               float* o, int i, int N, int n_res, float x, float y,
                                               float th, int lv, const float (&X)[4],
                                               const float (&Y)[4], const float (&TH)[4],

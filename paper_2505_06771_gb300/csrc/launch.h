@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "env_step.cuh"
 
 namespace rl {
@@ -18,6 +20,22 @@ cudaError_t launch_f32_large(const LaunchArgs<float>& a, int nmax, int lanes, in
                              int max_blocks, cudaStream_t st, bool reset);
 cudaError_t launch_f64(const LaunchArgs<double>& a, int nmax, int lanes, int block_threads,
                        int max_blocks, cudaStream_t st, bool reset);
+
+// One persistent launch over every class of an uneven batch (binary32).
+struct MultiClass {
+    int nmax, list_begin, count;
+};
+struct MultiArgs {
+    LaunchArgs<float> a;  // a.env_list: the class lists, concatenated
+    MultiClass cls[4];
+    const int4* items;    // (class, first index in the class list, envs)
+    int n_items;
+    unsigned* head;       // work-queue counter, zeroed by launch_multi
+    int fast;             // Navigation, scripted, no traces
+};
+cudaError_t launch_multi(const MultiArgs& m, unsigned class_mask, int max_blocks,
+                         cudaStream_t st);
+size_t multi_smem_bytes(unsigned class_mask);
 
 // Shared memory per team of a class.
 size_t team_smem_bytes(int precision, int nmax);

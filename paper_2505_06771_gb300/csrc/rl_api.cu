@@ -56,6 +56,12 @@ struct rl_env {
     // device scratch of rl_rollout_host
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // one persistent launch over all classes (binary32, uneven batches)
+    int use_multi = 0;
+    int n_items = 0;
+    int4* d_items = nullptr;
+    unsigned* d_head = nullptr;
+    unsigned class_mask = 0;
 };
 
 namespace {
@@ -194,6 +200,26 @@ rl_status do_rollout_launch(rl_env* h, int T, void* obs, void* rew, uint8_t* don
     a.io.obs = (R*)obs;
     a.io.reward = (R*)rew;
     a.io.done = done;
+    if constexpr (std::is_same<R, float>::value) {
+        if (h->use_multi && h->n_items > 0) {
+            rl::MultiArgs m;
+            std::memset(&m, 0, sizeof(m));
+            m.a = a;
+            m.a.env_list = h->d_lists;
+            for (int i = 0; i < h->ncls; ++i) {
+                m.cls[i].nmax = h->cls[i].nmax;
+                m.cls[i].list_begin = h->cls[i].begin;
+                m.cls[i].count = h->cls[i].count;
+            }
+            m.items = h->d_items;
+            m.n_items = h->n_items;
+            m.head = h->d_head;
+            m.fast = h->cfg.scenario == RL_SCEN_NAVIGATION ? 1 : 0;
+            cudaError_t e = rl::launch_multi(m, h->class_mask, 0, h->st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "rollout (one launch)");
+            return RL_OK;
+        }
+    }
     return run_all(h, a, false, "rollout");
 }
 
@@ -333,6 +359,21 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     }
     cudaError_t ce = cudaMalloc((void**)&h->d_lists, lists.size() * sizeof(int32_t));
     if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
+    // work items of the one-launch path, largest class first
+    std::vector<int4> items;
+    if (h->prec == 32 && h->ncls > 1) {
+        for (int c = h->ncls - 1; c >= 0; --c) {
+            const int tpb = 64 / h->cls[c].nmax;
+            for (int b = 0; b < h->cls[c].count; b += tpb)
+                items.push_back(make_int4(c, b, std::min(tpb, h->cls[c].count - b), 0));
+            h->class_mask |= 1u << (h->cls[c].nmax == 4 ? 0 : h->cls[c].nmax == 8 ? 1 : h->cls[c].nmax == 16 ? 2 : 3);
+        }
+        ce = cudaMalloc((void**)&h->d_items, items.size() * sizeof(int4) + 256);
+        if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
+        h->d_head = (unsigned*)((char*)h->d_items + ((items.size() * sizeof(int4) + 255) & ~(size_t)255));
+        h->n_items = (int)items.size();
+        h->use_multi = 1;
+    }
     ce = cudaMemsetAsync(h->d_img, 0, h->img_bytes, h->st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(h->d_lists, lists.data(), lists.size() * sizeof(int32_t),
@@ -342,6 +383,9 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
                              cudaMemcpyHostToDevice, h->st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(h->d_img + h->seg_off[S_OFF], h->h_off.data(), (E + 1) * 4,
+                             cudaMemcpyHostToDevice, h->st);
+    if (ce == cudaSuccess && h->n_items > 0)
+        ce = cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, h->st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
     if (ce != cudaSuccess) { rl_destroy(h); return RL_ERR_CUDA; }
@@ -435,6 +479,96 @@ rl_status rl_rollout_plain(rl_env* h, int32_t T, void* d_obs, void* d_rew, uint8
                 }
                 if (e != cudaSuccess) return cuda_fail(h, e, "plain step");
             }
+        }
+    }
+    return RL_OK;
+}
+
+rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
+    if (!h || T_probe < 1) return RL_ERR_ARG;
+    if (!h->cfg.scripted) return fail(h, RL_ERR_STATE, "rl_tune: the handle takes policy actions");
+    // the probes run from a saved copy of the state, which is restored afterwards
+    void* saved = nullptr;
+    cudaError_t e = cudaMalloc(&saved, h->img_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, RL_ERR_OOM, "rl_tune: state copy"); }
+    e = cudaMemcpyAsync(saved, h->d_img, h->img_bytes, cudaMemcpyDeviceToDevice, h->st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    auto probe = [&](float& ms) -> rl_status {
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaError_t ee = cudaMemcpyAsync(h->d_img, saved, h->img_bytes, cudaMemcpyDeviceToDevice, h->st);
+            if (ee != cudaSuccess) return cuda_fail(h, ee, "rl_tune");
+            cudaEventRecord(e0, h->st);
+            rl_status st = rollout_enqueue(h, T_probe, nullptr, nullptr, nullptr);
+            if (st != RL_OK) return st;
+            cudaEventRecord(e1, h->st);
+            ee = cudaEventSynchronize(e1);
+            if (ee != cudaSuccess) return cuda_fail(h, ee, "rl_tune");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
+        }
+        ms = best;
+        return RL_OK;
+    };
+    rl_status st = e == cudaSuccess ? RL_OK : cuda_fail(h, e, "rl_tune");
+    const int bts[3] = {32, 64, 128};
+    // per class: the fastest (lanes, block) with only that class launched
+    const int keep_multi = h->use_multi;
+    h->use_multi = 0;
+    for (int c = 0; c < h->ncls && st == RL_OK; ++c) {
+        const int nc = h->ncls;
+        Class all[4];
+        for (int i = 0; i < nc; ++i) all[i] = h->cls[i];
+        h->cls[0] = all[c];
+        h->ncls = 1;
+        const unsigned ok = rl::supported_lanes(h->prec, all[c].nmax);
+        float best = 1e30f;
+        Class pick = all[c];
+        for (int lanes = 1; lanes <= 32 && st == RL_OK; lanes <<= 1) {
+            if (!(ok & (unsigned)lanes)) continue;
+            for (int b = 0; b < 3 && st == RL_OK; ++b) {
+                if (bts[b] < lanes) continue;
+                h->cls[0].lanes = lanes;
+                h->cls[0].block_threads = bts[b];
+                float ms = 0.f;
+                st = probe(ms);
+                if (st == RL_OK && ms < best) { best = ms; pick = h->cls[0]; }
+            }
+        }
+        for (int i = 0; i < nc; ++i) h->cls[i] = all[i];
+        h->ncls = nc;
+        h->cls[c] = pick;
+    }
+    // uneven batches: one launch over every class, or one launch per class
+    if (st == RL_OK && h->n_items > 0) {
+        float per_class = 0.f, one = 0.f;
+        h->use_multi = 0;
+        st = probe(per_class);
+        if (st == RL_OK) {
+            h->use_multi = 1;
+            st = probe(one);
+        }
+        h->use_multi = (st == RL_OK && one <= per_class) ? 1 : 0;
+    } else {
+        h->use_multi = keep_multi;
+    }
+    cudaError_t er = cudaMemcpyAsync(h->d_img, saved, h->img_bytes, cudaMemcpyDeviceToDevice, h->st);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(h->st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(saved);
+    drop_graph(h);
+    if (st != RL_OK) return st;
+    if (er != cudaSuccess) return cuda_fail(h, er, "rl_tune restore");
+    if (h_choice) {
+        h_choice[0] = h->use_multi;
+        for (int c = 0; c < 4; ++c) {
+            h_choice[1 + 3 * c] = c < h->ncls ? h->cls[c].nmax : 0;
+            h_choice[2 + 3 * c] = c < h->ncls ? h->cls[c].lanes : 0;
+            h_choice[3 + 3 * c] = c < h->ncls ? h->cls[c].block_threads : 0;
         }
     }
     return RL_OK;
@@ -553,6 +687,7 @@ void rl_destroy(rl_env* h) {
     drop_graph(h);
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_lists) cudaFree(h->d_lists);
+    if (h->d_items) cudaFree(h->d_items);
     if (h->d_img) cudaFree(h->d_img);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;

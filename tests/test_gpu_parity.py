@@ -279,3 +279,53 @@ def test_argument_errors(rl):
         rl.Env(dict(g, episode_len=0), 8, 4, 0)
     with pytest.raises(rl.RLError):
         rl.Env(g, 8, 33, 0)
+
+
+@pytest.mark.parametrize("scenario", [0, 1])
+def test_uneven_one_launch_matches_steps(rl, scenario):
+    """Uneven robot counts (2..10, every class up to 16 robots) in one persistent launch match
+    one step at a time through the per-class launches: done flags and integer state exactly,
+    values to rounding (the same device code compiled into two kernels may contract multiply-
+    adds differently)."""
+    from synth_inputs import uneven_robot_counts
+    n = uneven_robot_counts(8, 333, 2, 10)
+    g, _ = make_pair(scenario, 10, episode_len=25)
+    T = 40
+    a = rl.Env(g, 333, n, 31)
+    bt = _alloc(a, T)
+    a.rollout(T, **bt)
+    b = rl.Env(g, 333, n, 31)
+    worst = 0.0
+    for t in range(T):
+        bs = _alloc(b)
+        b.step(obs=bs["obs"], reward=bs["reward"], done=bs["done"])
+        worst = max(worst, (bs["obs"] - bt["obs"][t]).abs().max().item(),
+                    (bs["reward"] - bt["reward"][t]).abs().max().item())
+        assert torch.equal(bs["done"], bt["done"][t]), f"done differs at step {t}"
+    sa, sb = a.state_arrays(), b.state_arrays()
+    print(f"\none launch vs steps, scenario {scenario}: max |diff| {worst:.3e}")
+    for k in ("t", "ep", "level", "qactive", "counters"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert worst < 1e-4
+    a.close()
+    b.close()
+
+
+def test_tuner_keeps_state_and_results(rl):
+    n = [2, 3, 4, 6, 8, 12, 16, 20] * 16
+    g, _ = make_pair(0, 20)
+    env = rl.Env(g, len(n), n, 5)
+    ref = rl.Env(g, len(n), n, 5)
+    before = env.get_state()
+    choice = env.tune(10)
+    print(f"\ntuner choice: {choice}")
+    assert env.get_state() == before
+    assert len(choice["classes"]) == 4
+    T = 30
+    b1, b2 = _alloc(env, T), _alloc(ref, T)
+    env.rollout(T, **b1)
+    ref.rollout(T, **b2)
+    assert torch.equal(b1["done"], b2["done"])
+    assert (b1["obs"] - b2["obs"]).abs().max().item() < 1e-4
+    env.close()
+    ref.close()
