@@ -200,6 +200,49 @@ rl_status rl_rollout_noalloc(const rl_config* cfg, int32_t n_envs, int32_t n_rob
                              uint8_t* d_done_traj, void* stream);
 size_t    rl_noalloc_state_bytes(const rl_config* cfg, int32_t n_envs, int32_t n_robots);
 
+/* ---- Serving: continuous batching of rollout requests ------------------------------------
+   A server runs scripted rollout requests (n_envs environments of n_robots robots, horizon
+   steps, seed) with the configuration given at creation.  An engine thread admits queued
+   requests in arrival order whenever one of max_slots slots is free and the device bytes the
+   request holds fit in what the budget has left; each admitted request runs as one persistent
+   rollout launch on its slot's stream, so requests admitted at different times run on the GPU
+   at the same time.  Its environment state stays on the device for the whole horizon; only the
+   per-env returns and counters come back.  A request's result is the same alone or in any mix
+   (the same kernels on the same data).  Latency = finish - submit on the host steady clock. */
+typedef struct rl_server rl_server;
+typedef struct {
+    int32_t n_envs;     /* >= 1 */
+    int32_t n_robots;   /* 1..32 (and <= the config's n_max when that is set) */
+    int32_t horizon;    /* steps, >= 0 */
+    uint64_t seed;
+} rl_request;
+typedef struct {
+    uint64_t id;
+    int32_t status;     /* 0 queued, 1 running, 2 done, 3 failed */
+    int32_t n_envs, n_robots, horizon;
+    double submit_s, start_s, finish_s;   /* seconds since the server was created */
+    double mean_return;                   /* mean over envs of the summed team reward */
+    int32_t counters[RL_NCOUNT];          /* summed over the request's envs */
+} rl_result;
+
+/* hbm_budget_bytes: device bytes all running requests may hold together.  The server uses the
+   current device. */
+rl_status rl_server_create(const rl_config* cfg, size_t hbm_budget_bytes, int32_t max_slots,
+                           rl_server** out);
+/* Queue a request; *id identifies it.  RL_ERR_BUDGET if it can never fit the budget,
+   RL_ERR_ARG on bad sizes.  Thread-safe; returns at once. */
+rl_status rl_server_submit(rl_server* srv, const rl_request* req, uint64_t* id);
+/* Status of a request; h_returns (NULL or n_envs floats) gets the per-env returns once done.
+   RL_ERR_ARG for an unknown id, RL_ERR_CUDA if the request failed. */
+rl_status rl_server_result(rl_server* srv, uint64_t id, rl_result* out, float* h_returns);
+/* out[6]: bytes in use, peak bytes in use, requests done, running, queued, env-steps done. */
+rl_status rl_server_stats(rl_server* srv, int64_t* out);
+/* Wait (host side, at most timeout_s seconds) until every submitted request has finished;
+   RL_ERR_TIMEOUT if they have not. */
+rl_status rl_server_drain(rl_server* srv, double timeout_s);
+/* Stop the engine, wait for running requests, free everything.  NULL-safe. */
+rl_status rl_server_destroy(rl_server* srv);
+
 int32_t     rl_obs_dim(const rl_env* env);
 int32_t     rl_n_envs(const rl_env* env);
 int32_t     rl_total_robots(const rl_env* env);

@@ -19,8 +19,8 @@ import numpy as np
 from .build import LIB as LIB_PATH
 from .build import build
 
-__all__ = ["build", "lib", "config_default", "Env", "RLError", "NAVIGATION", "FORAGING",
-           "COUNTERS", "exported_symbols"]
+__all__ = ["build", "lib", "config_default", "Env", "Server", "RLError", "NAVIGATION",
+           "FORAGING", "COUNTERS", "exported_symbols", "rollout_noalloc", "noalloc_state_bytes"]
 
 NAVIGATION, FORAGING = 0, 1
 COUNTERS = ("collisions", "oob", "success", "qp_active", "qp_flagged", "qp_infeasible",
@@ -46,6 +46,19 @@ class RLConfig(ctypes.Structure):
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
                  "near_frac", "near_dmin", "near_dmax", "h_flag")]
+
+
+class RLRequest(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_int32), ("n_robots", ctypes.c_int32),
+                ("horizon", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class RLResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_envs", ctypes.c_int32),
+                ("n_robots", ctypes.c_int32), ("horizon", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double), ("mean_return", ctypes.c_double),
+                ("counters", ctypes.c_int32 * 8)]
 
 
 class RLStepIO(ctypes.Structure):
@@ -100,6 +113,13 @@ def lib():
         L.rl_destroy.argtypes = [vp]
         L.rl_destroy.restype = None
         L.rl_tune.argtypes = [vp, i32, vp]
+        L.rl_server_create.argtypes = [ctypes.POINTER(RLConfig), sz, i32, ctypes.POINTER(vp)]
+        L.rl_server_submit.argtypes = [vp, ctypes.POINTER(RLRequest),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.rl_server_result.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(RLResult), vp]
+        L.rl_server_stats.argtypes = [vp, vp]
+        L.rl_server_drain.argtypes = [vp, ctypes.c_double]
+        L.rl_server_destroy.argtypes = [vp]
         L.rl_rollout_noalloc.argtypes = [ctypes.POINTER(RLConfig), i32, i32, u64, i32, vp, vp, vp,
                                          vp]
         L.rl_noalloc_state_bytes.argtypes = [ctypes.POINTER(RLConfig), i32, i32]
@@ -303,6 +323,68 @@ def rollout_noalloc(cfg: dict, n_envs: int, n_robots: int, seed: int, T: int, ob
                               ctypes.c_void_p(s.cuda_stream))
     if st:
         raise RLError(st, "rl_rollout_noalloc")
+
+
+class Server:
+    """Continuous-batching rollout server (rl_server_*) on the current CUDA device."""
+
+    def __init__(self, cfg: dict, hbm_budget_bytes: int, max_slots: int = 16):
+        import torch
+        torch.cuda.current_device()
+        self._L = lib()
+        h = ctypes.c_void_p()
+        st = self._L.rl_server_create(ctypes.byref(_to_struct(cfg)), int(hbm_budget_bytes),
+                                      max_slots, ctypes.byref(h))
+        if st:
+            raise RLError(st, "rl_server_create")
+        self._h = h
+
+    def submit(self, n_envs: int, n_robots: int, horizon: int, seed: int) -> int:
+        rid = ctypes.c_uint64()
+        st = self._L.rl_server_submit(self._h, ctypes.byref(RLRequest(n_envs, n_robots, horizon,
+                                                                      seed)), ctypes.byref(rid))
+        if st:
+            raise RLError(st, "rl_server_submit")
+        return int(rid.value)
+
+    def result(self, rid: int, returns: bool = False):
+        r = RLResult()
+        buf = None
+        st = self._L.rl_server_result(self._h, rid, ctypes.byref(r), None)
+        if st == 0 and returns and r.status == 2:
+            buf = np.zeros(r.n_envs, np.float32)
+            st = self._L.rl_server_result(self._h, rid, ctypes.byref(r), buf.ctypes.data)
+        if st:
+            raise RLError(st, "rl_server_result")
+        d = {k: getattr(r, k) for k, _ in RLResult._fields_ if k != "counters"}
+        d["counters"] = list(r.counters)
+        d["latency_s"] = r.finish_s - r.submit_s
+        if buf is not None:
+            d["returns"] = buf
+        return d
+
+    def stats(self) -> dict:
+        out = np.zeros(6, np.int64)
+        self._L.rl_server_stats(self._h, out.ctypes.data)
+        return dict(used=int(out[0]), peak=int(out[1]), done=int(out[2]), running=int(out[3]),
+                    queued=int(out[4]), env_steps=int(out[5]))
+
+    def drain(self, timeout_s: float) -> bool:
+        st = self._L.rl_server_drain(self._h, timeout_s)
+        if st not in (0, 5):
+            raise RLError(st, "rl_server_drain")
+        return st == 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def noalloc_state_bytes(cfg: dict, n_envs: int, n_robots: int) -> int:

@@ -512,6 +512,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     const int nd = (N - 1) / 2;
     const int ndi = own ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
     const float* acts = actions;
+    float ret_acc = 0.f;
 
     for (int step = 0; step < A.T; ++step) {
         // ---- projected point and nominal SI velocity of the own robot
@@ -701,7 +702,9 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
             if (A.io.reward) A.io.reward[(long long)step * A.io.E + e] = rew;
             if (A.io.done) A.io.done[(long long)step * A.io.E + e] = done ? 1 : 0;
         }
+        ret_acc += rew;
     }
+    if (A.io.ret && i == 0) A.io.ret[e] = ret_acc;
     if (own) {
         A.s.x[row] = x; A.s.y[row] = y; A.s.th[row] = th;
         A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.level[row] = lv;

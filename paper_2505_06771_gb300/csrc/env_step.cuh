@@ -73,6 +73,7 @@ struct StepIO {
     R* u_star;
     R* vw;
     int32_t* qp_info;  // [E][4]
+    R* ret;            // [E] sum of the rewards of this launch (serving), or NULL
     long long obs_step;  // rows * obs_dim
     int E;
     int obs_dim;
@@ -789,6 +790,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
     for (int c = 0; c < kNCount; ++c) cnt[c] = (tm.lane == 0) ? A.s.counters[e * kNCount + c] : 0;
     tm.sync();
 
+    R ret_acc = (R)0;
     for (int step = 0; step < A.T; ++step) {
         // ---- projected points and nominal SI velocity
         R dold[RPL], u0x[RPL], u0y[RPL];
@@ -1078,7 +1080,9 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
             if (A.io.reward) A.io.reward[(long long)step * A.io.E + e] = rew;
             if (A.io.done) A.io.done[(long long)step * A.io.E + e] = done ? 1 : 0;
         }
+        ret_acc += rew;
     }
+    if (A.io.ret && tm.lane == 0) A.io.ret[e] = ret_acc;
 
     // ---- state back to global memory
 #pragma unroll

@@ -2,10 +2,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/rl.h"
@@ -223,6 +229,34 @@ rl_status do_rollout_launch(rl_env* h, int T, void* obs, void* rew, uint8_t* don
     return run_all(h, a, false, "rollout");
 }
 
+template <typename R>
+rl_status do_rollout_returns(rl_env* h, int T, void* ret) {
+    rl::LaunchArgs<R> a;
+    fill_args(h, a);
+    a.T = T;
+    a.io.ret = (R*)ret;
+    if constexpr (std::is_same<R, float>::value) {
+        if (h->use_multi && h->n_items > 0) {
+            rl::MultiArgs m;
+            std::memset(&m, 0, sizeof(m));
+            m.a = a;
+            m.a.env_list = h->d_lists;
+            for (int i = 0; i < h->ncls; ++i) {
+                m.cls[i].nmax = h->cls[i].nmax;
+                m.cls[i].list_begin = h->cls[i].begin;
+                m.cls[i].count = h->cls[i].count;
+            }
+            m.items = h->d_items;
+            m.n_items = h->n_items;
+            m.head = h->d_head;
+            m.fast = h->cfg.scenario == RL_SCEN_NAVIGATION ? 1 : 0;
+            cudaError_t e = rl::launch_multi(m, h->class_mask, 0, h->st);
+            return e == cudaSuccess ? RL_OK : cuda_fail(h, e, "serving rollout");
+        }
+    }
+    return run_all(h, a, false, "serving rollout");
+}
+
 rl_status rollout_enqueue(rl_env* h, int T, void* obs, void* rew, uint8_t* done) {
     return h->prec == 64 ? do_rollout_launch<double>(h, T, obs, rew, done)
                          : do_rollout_launch<float>(h, T, obs, rew, done);
@@ -329,7 +363,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         if (e != cudaSuccess) { delete h; return RL_ERR_CUDA; }
         h->own_stream = true;
     }
-    if (cudaMalloc((void**)&h->d_img, h->img_bytes) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&h->d_img, h->img_bytes, h->st) != cudaSuccess) {
         cudaGetLastError();
         rl_destroy(h);
         return RL_ERR_OOM;
@@ -357,7 +391,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         }
         h->cls[h->ncls++] = k;
     }
-    cudaError_t ce = cudaMalloc((void**)&h->d_lists, lists.size() * sizeof(int32_t));
+    cudaError_t ce = cudaMallocAsync((void**)&h->d_lists, lists.size() * sizeof(int32_t), h->st);
     if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
     // work items of the one-launch path, largest class first
     std::vector<int4> items;
@@ -368,7 +402,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
                 items.push_back(make_int4(c, b, std::min(tpb, h->cls[c].count - b), 0));
             h->class_mask |= 1u << (h->cls[c].nmax == 4 ? 0 : h->cls[c].nmax == 8 ? 1 : h->cls[c].nmax == 16 ? 2 : 3);
         }
-        ce = cudaMalloc((void**)&h->d_items, items.size() * sizeof(int4) + 256);
+        ce = cudaMallocAsync((void**)&h->d_items, items.size() * sizeof(int4) + 256, h->st);
         if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
         h->d_head = (unsigned*)((char*)h->d_items + ((items.size() * sizeof(int4) + 255) & ~(size_t)255));
         h->n_items = (int)items.size();
@@ -489,7 +523,7 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     if (!h->cfg.scripted) return fail(h, RL_ERR_STATE, "rl_tune: the handle takes policy actions");
     // the probes run from a saved copy of the state, which is restored afterwards
     void* saved = nullptr;
-    cudaError_t e = cudaMalloc(&saved, h->img_bytes);
+    cudaError_t e = cudaMallocAsync(&saved, h->img_bytes, h->st);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(h, RL_ERR_OOM, "rl_tune: state copy"); }
     e = cudaMemcpyAsync(saved, h->d_img, h->img_bytes, cudaMemcpyDeviceToDevice, h->st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -559,7 +593,7 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     if (er == cudaSuccess) er = cudaStreamSynchronize(h->st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(saved);
+    cudaFreeAsync(saved, h->st);
     drop_graph(h);
     if (st != RL_OK) return st;
     if (er != cudaSuccess) return cuda_fail(h, er, "rl_tune restore");
@@ -635,9 +669,9 @@ rl_status rl_rollout_host(rl_env* h, const void* h_state, int32_t T, void* h_obs
     const size_t db = h_done ? (size_t)T * h->E : 0;
     const size_t need = ((ob + 255) & ~(size_t)255) + ((rb + 255) & ~(size_t)255) + db + 256;
     if (need > h->scratch_bytes) {
-        if (h->d_scratch) { cudaFree(h->d_scratch); h->d_scratch = nullptr; h->scratch_bytes = 0; }
+        if (h->d_scratch) { cudaFreeAsync(h->d_scratch, h->st); h->d_scratch = nullptr; h->scratch_bytes = 0; }
         drop_graph(h);
-        if (cudaMalloc(&h->d_scratch, need) != cudaSuccess) {
+        if (cudaMallocAsync(&h->d_scratch, need, h->st) != cudaSuccess) {
             cudaGetLastError();
             return fail(h, RL_ERR_OOM, "rollout_host: scratch allocation");
         }
@@ -685,12 +719,307 @@ void rl_destroy(rl_env* h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
     drop_graph(h);
-    if (h->d_scratch) cudaFree(h->d_scratch);
-    if (h->d_lists) cudaFree(h->d_lists);
-    if (h->d_items) cudaFree(h->d_items);
-    if (h->d_img) cudaFree(h->d_img);
+    // stream-ordered frees: no device-wide synchronisation
+    if (h->d_scratch) cudaFreeAsync(h->d_scratch, h->st);
+    if (h->d_lists) cudaFreeAsync(h->d_lists, h->st);
+    if (h->d_items) cudaFreeAsync(h->d_items, h->st);
+    if (h->d_img) cudaFreeAsync(h->d_img, h->st);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
+}
+
+}  // extern "C"
+
+// ================================================================================================
+// Serving: continuous batching of rollout requests under a device-memory budget
+// ================================================================================================
+namespace {
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Device bytes a request holds while it runs (state image, class lists, work items, returns).
+size_t request_bytes(const rl_config& c, const rl_request& r) {
+    const size_t E = (size_t)r.n_envs, rows = E * (size_t)r.n_robots;
+    const size_t es = c.precision == RL_PREC_F64 ? 8 : 4;
+    const size_t RM = c.scenario == RL_SCEN_FORAGING ? E * (size_t)c.r_max : 0;
+    auto a = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    return 5 * a(rows * es) + a(rows * 4) + 3 * a(E * 4) + 2 * a(RM * es) + 2 * a(RM * 4) +
+           a(E * rl::kNCount * 4) + a(E * 4) + a((E + 1) * 4) + a(E * 4) + a(E * es) + 4096;
+}
+
+struct SrvReq {
+    uint64_t id;
+    rl_request r;
+    double t_submit;
+    size_t bytes;
+};
+
+struct SrvSlot {
+    bool busy = false;
+    SrvReq req{};
+    rl_env* env = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    void* d_ret = nullptr;
+    double t_start = 0.0;
+};
+
+struct SrvResult {
+    int status = 0;  // 0 queued, 1 running, 2 done, 3 failed
+    rl_request r{};
+    double t_submit = 0, t_start = 0, t_finish = 0;
+    std::vector<float> returns;
+    int32_t counters[RL_NCOUNT] = {};
+};
+
+}  // namespace
+
+struct rl_server {
+    rl_config cfg;
+    size_t budget = 0, used = 0, peak = 0;
+    int device = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<SrvReq> queue;
+    std::vector<SrvSlot> slots;
+    std::unordered_map<uint64_t, SrvResult> results;
+    uint64_t next_id = 1;
+    int64_t n_done = 0, env_steps_done = 0;
+    bool stop = false;
+    std::string err;
+    std::thread engine;
+};
+
+namespace {
+
+// Start a request in a free slot (engine thread, lock held).
+bool srv_start(rl_server* S, SrvSlot& sl, const SrvReq& q) {
+    rl_config c = S->cfg;
+    c.scripted = 1;
+    rl_env* env = nullptr;
+    if (rl_create(&c, q.r.n_envs, nullptr, q.r.n_robots, q.r.seed, sl.st, &env) != RL_OK) return false;
+    const size_t es = c.precision == RL_PREC_F64 ? 8 : 4;
+    if (cudaMallocAsync(&sl.d_ret, (size_t)q.r.n_envs * es, sl.st) != cudaSuccess) {
+        cudaGetLastError();
+        rl_destroy(env);
+        return false;
+    }
+    rl_status st = c.precision == RL_PREC_F64 ? do_rollout_returns<double>(env, q.r.horizon, sl.d_ret)
+                                              : do_rollout_returns<float>(env, q.r.horizon, sl.d_ret);
+    if (st != RL_OK || cudaEventRecord(sl.ev, sl.st) != cudaSuccess) {
+        cudaFreeAsync(sl.d_ret, sl.st);
+        rl_destroy(env);
+        return false;
+    }
+    sl.env = env;
+    sl.req = q;
+    sl.busy = true;
+    sl.t_start = now_s(S->t0);
+    return true;
+}
+
+// Collect a finished request (engine thread, lock held).
+void srv_finish(rl_server* S, SrvSlot& sl, bool ok) {
+    SrvResult& R = S->results[sl.req.id];
+    R.t_finish = now_s(S->t0);
+    R.t_start = sl.t_start;
+    R.status = 3;
+    if (ok) {
+        const size_t E = (size_t)sl.req.r.n_envs;
+        R.returns.assign(E, 0.f);
+        std::vector<int32_t> cnt(E * RL_NCOUNT);
+        bool good = rl_get_counters(sl.env, cnt.data()) == RL_OK;
+        if (S->cfg.precision == RL_PREC_F64) {
+            std::vector<double> tmp(E);
+            good = good && cudaMemcpyAsync(tmp.data(), sl.d_ret, E * 8, cudaMemcpyDeviceToHost, sl.st) == cudaSuccess;
+            good = good && cudaStreamSynchronize(sl.st) == cudaSuccess;
+            for (size_t i = 0; i < E; ++i) R.returns[i] = (float)tmp[i];
+        } else {
+            good = good && cudaMemcpyAsync(R.returns.data(), sl.d_ret, E * 4, cudaMemcpyDeviceToHost, sl.st) == cudaSuccess;
+            good = good && cudaStreamSynchronize(sl.st) == cudaSuccess;
+        }
+        for (size_t e = 0; e < E; ++e)
+            for (int k = 0; k < RL_NCOUNT; ++k) R.counters[k] += cnt[e * RL_NCOUNT + k];
+        if (good) {
+            R.status = 2;
+            S->n_done += 1;
+            S->env_steps_done += (int64_t)sl.req.r.n_envs * sl.req.r.horizon;
+        }
+    }
+    cudaFreeAsync(sl.d_ret, sl.st);
+    sl.d_ret = nullptr;
+    rl_destroy(sl.env);
+    sl.env = nullptr;
+    sl.busy = false;
+    S->used -= sl.req.bytes;
+}
+
+void srv_engine(rl_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool busy = false;
+        for (SrvSlot& sl : S->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev);
+            if (q == cudaSuccess) srv_finish(S, sl, true);
+            else if (q != cudaErrorNotReady) { cudaGetLastError(); srv_finish(S, sl, false); }
+            else busy = true;
+        }
+        // admit in arrival order while a slot and the budget allow
+        while (!S->queue.empty() && S->used + S->queue.front().bytes <= S->budget) {
+            SrvSlot* free_slot = nullptr;
+            for (SrvSlot& sl : S->slots)
+                if (!sl.busy) { free_slot = &sl; break; }
+            if (!free_slot) break;
+            SrvReq q = S->queue.front();
+            S->queue.pop_front();
+            S->used += q.bytes;
+            S->peak = std::max(S->peak, S->used);
+            S->results[q.id].status = 1;
+            if (srv_start(S, *free_slot, q)) {
+                busy = true;
+            } else {
+                S->used -= q.bytes;
+                SrvResult& R = S->results[q.id];
+                R.status = 3;
+                R.t_finish = now_s(S->t0);
+            }
+        }
+        S->cv.notify_all();
+        if (busy) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        } else {
+            S->cv.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+rl_status rl_server_create(const rl_config* cfg, size_t hbm_budget_bytes, int32_t max_slots,
+                           rl_server** out) {
+    if (!cfg || !out || max_slots < 1 || hbm_budget_bytes == 0) return RL_ERR_ARG;
+    std::string why;
+    if (!valid_cfg(*cfg, why)) return RL_ERR_ARG;
+    rl_server* S = new (std::nothrow) rl_server();
+    if (!S) return RL_ERR_OOM;
+    S->cfg = *cfg;
+    S->budget = hbm_budget_bytes;
+    S->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return RL_ERR_CUDA; }
+    S->slots.resize(max_slots);
+    for (SrvSlot& sl : S->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            rl_server_destroy(S);
+            return RL_ERR_CUDA;
+        }
+    }
+    S->engine = std::thread(srv_engine, S);
+    *out = S;
+    return RL_OK;
+}
+
+rl_status rl_server_submit(rl_server* S, const rl_request* r, uint64_t* id) {
+    if (!S || !r || !id) return RL_ERR_ARG;
+    if (r->n_envs < 1 || r->n_robots < 1 || r->n_robots > rl::kMaxRobots || r->horizon < 0)
+        return RL_ERR_ARG;
+    if (S->cfg.n_max > 0 && r->n_robots > S->cfg.n_max) return RL_ERR_ARG;
+    const size_t b = request_bytes(S->cfg, *r);
+    if (b > S->budget) return RL_ERR_BUDGET;
+    std::lock_guard<std::mutex> lk(S->mu);
+    SrvReq q{S->next_id++, *r, now_s(S->t0), b};
+    SrvResult& R = S->results[q.id];
+    R.status = 0;
+    R.r = *r;
+    R.t_submit = q.t_submit;
+    S->queue.push_back(q);
+    *id = q.id;
+    S->cv.notify_all();
+    return RL_OK;
+}
+
+rl_status rl_server_result(rl_server* S, uint64_t id, rl_result* out, float* h_returns) {
+    if (!S || !out) return RL_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(id);
+    if (it == S->results.end()) return RL_ERR_ARG;
+    const SrvResult& R = it->second;
+    std::memset(out, 0, sizeof(*out));
+    out->id = id;
+    out->status = R.status;
+    out->n_envs = R.r.n_envs;
+    out->n_robots = R.r.n_robots;
+    out->horizon = R.r.horizon;
+    out->submit_s = R.t_submit;
+    out->start_s = R.t_start;
+    out->finish_s = R.t_finish;
+    for (int k = 0; k < RL_NCOUNT; ++k) out->counters[k] = R.counters[k];
+    double sum = 0.0;
+    for (float v : R.returns) sum += v;
+    out->mean_return = R.returns.empty() ? 0.0 : sum / (double)R.returns.size();
+    if (h_returns && R.status == 2) std::memcpy(h_returns, R.returns.data(), R.returns.size() * 4);
+    return R.status == 3 ? RL_ERR_CUDA : RL_OK;
+}
+
+rl_status rl_server_stats(rl_server* S, int64_t* out) {
+    if (!S || !out) return RL_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    int64_t running = 0;
+    for (const SrvSlot& sl : S->slots) running += sl.busy ? 1 : 0;
+    out[0] = (int64_t)S->used;
+    out[1] = (int64_t)S->peak;
+    out[2] = S->n_done;
+    out[3] = running;
+    out[4] = (int64_t)S->queue.size();
+    out[5] = S->env_steps_done;
+    return RL_OK;
+}
+
+rl_status rl_server_drain(rl_server* S, double timeout_s) {
+    if (!S) return RL_ERR_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::microseconds((int64_t)(timeout_s * 1e6));
+    for (;;) {
+        bool idle = S->queue.empty();
+        for (const SrvSlot& sl : S->slots) idle = idle && !sl.busy;
+        if (idle) return RL_OK;
+        if (std::chrono::steady_clock::now() >= deadline) return RL_ERR_TIMEOUT;
+        S->cv.wait_until(lk, deadline);
+    }
+}
+
+rl_status rl_server_destroy(rl_server* S) {
+    if (!S) return RL_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->engine.joinable()) S->engine.join();
+    for (SrvSlot& sl : S->slots) {
+        if (sl.busy) {
+            cudaStreamSynchronize(sl.st);
+            if (sl.d_ret) cudaFreeAsync(sl.d_ret, sl.st);
+            rl_destroy(sl.env);
+        }
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) {
+            cudaStreamSynchronize(sl.st);
+            cudaStreamDestroy(sl.st);
+        }
+    }
+    delete S;
+    return RL_OK;
 }
 
 }  // extern "C"
