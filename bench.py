@@ -1,14 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the batched CBF-QP multi-robot environment step on GB300.
 
-Workload (one bench step): the Navigation batch of 4096 environments x 4 robots, 1000 scripted
-steps (10 episodes of 100 steps), binary32, run by rl_rollout as one CUDA-graph replay of the
-persistent kernel, streaming observations [1000, 16384, 14], rewards and done flags (938 MB)
-to HBM.  Reported: env-steps/s (and robot-steps/s), the plain one-launch-per-env-per-step form
-of the same step, p50/p99 rollout latency, the HBM roofline fraction of the rollout kernel, the
-end-to-end rate through host buffers, and the FP64 CPU oracle timed on the host cores.
+Default workload (one bench step): the Navigation batch of 4096 environments x 4 robots,
+1000 scripted steps (10 episodes of 100 steps), binary32, run by rl_rollout as one CUDA-graph
+replay of the persistent kernel, streaming observations [1000, 16384, 14], rewards and done
+flags (938 MB) to HBM.  Reported: env-steps/s (and robot-steps/s), the plain one-launch-per-env-
+per-step form of the same step, p50/p99 rollout latency, the HBM roofline fraction of the
+rollout kernel, the end-to-end rate through host buffers, and the FP64 CPU oracle timed on the
+host cores.
 
-python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Other workloads (--workload): tiny (16 x 4 x 100, binary64), uneven (8192 envs of 2..10 robots,
+Foraging, 500 steps, one persistent launch), largen (1024 x 20 x 300, 30% near pairs, binary32
+with binary64 re-solve), serving (Poisson arrivals, 60 GB budget, p50/p99 latency).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
 Under torchrun each rank runs its own batch (weak scaling, no data-path collective).
 """
 from __future__ import annotations
@@ -30,26 +35,38 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s with CBF-QP filter vs plain per-env form; p50/p99 rollout latency"
-E, N, T = 4096, 4, 1000
-WORKLOAD = "navigation: 4096 envs x 4 robots x 1000 steps, scripted nominal control, fp32"
+
+WORKLOADS = {
+    "nav": dict(desc="navigation: 4096 envs x 4 robots x 1000 steps, scripted nominal control, fp32",
+                scenario=0, E=4096, N=4, T=1000, precision=32, near=0.0, n_max=4),
+    "tiny": dict(desc="navigation: 16 envs x 4 robots x 100 steps, fp64",
+                 scenario=0, E=16, N=4, T=100, precision=64, near=0.0, n_max=4),
+    "uneven": dict(desc="foraging: 8192 envs x U{2..10} robots x 500 steps, 2-6 resources, fp32, "
+                        "one persistent launch",
+                   scenario=1, E=8192, N="uneven", T=500, precision=32, near=0.0, n_max=10),
+    "largen": dict(desc="navigation: 1024 envs x 20 robots x 300 steps, 30% near pairs, fp32 + "
+                        "fp64 re-solve of flagged QPs",
+                   scenario=0, E=1024, N=20, T=300, precision=32, near=0.3, n_max=20),
+}
 
 
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="nav", choices=list(WORKLOADS) + ["serving"])
+    p.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form leg")
+    p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     return p.parse_args()
 
 
 def _dist():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def _source_hash() -> str:
@@ -60,9 +77,9 @@ def _source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic():
+def _ncu_traffic(workload: str):
     """dram bytes per launch recorded from an ncu capture of this exact kernel source."""
-    path = os.path.join(ROOT, "profiles", "ncu_rollout_nav4096x4.md")
+    path = os.path.join(ROOT, "profiles", f"ncu_rollout_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -82,7 +99,7 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (100 ms) during the timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -97,7 +114,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -138,23 +155,38 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _cpu_baseline(budget_s: float = 20.0):
-    """The FP64 oracle on the host cores: up to the full workload in 100-step chunks, stopping
+def _robots(w):
+    from synth_inputs import uneven_robot_counts
+    import numpy as np
+    if w["N"] == "uneven":
+        return uneven_robot_counts(0, w["E"], 2, 10)
+    return np.full(w["E"], w["N"], np.int32)
+
+
+def _oracle_cfg(w):
+    import oracle
+    return oracle.default_cfg(w["scenario"], n_max=w["n_max"], near_frac=w["near"])
+
+
+def _cpu_baseline(w, budget_s: float = 20.0):
+    """The FP64 oracle on the host cores: the workload in chunks of up to 100 steps, stopping
     after budget_s seconds; env-steps/s over the chunks done."""
     import oracle
     threads = os.cpu_count() or 1
-    c = oracle.default_cfg(oracle.NAV, n_max=N)
-    s = oracle.reset(c, 0, [N] * E)
+    n = _robots(w)
+    c = _oracle_cfg(w)
+    s = oracle.reset(c, 0, n)
+    chunk = min(100, w["T"])
     done_steps, t0 = 0, time.perf_counter()
-    while done_steps < T:
-        oracle.rollout(c, 0, s, 100, want_obs=True, threads=threads)
-        done_steps += 100
+    while done_steps < w["T"]:
+        oracle.rollout(c, 0, s, chunk, want_obs=True, threads=threads)
+        done_steps += chunk
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": E * done_steps / dt, "unit": "env-steps/s", "cores": threads,
+    return {"value": w["E"] * done_steps / dt, "unit": "env-steps/s", "cores": threads,
             "kind": "oracle",
-            "sample": f"{E} envs x {N} robots x {done_steps} steps of the same workload "
+            "sample": f"{w['E']} envs x {done_steps} of {w['T']} steps of the same workload "
                       f"(FP64 C oracle, OpenMP over envs, observations written)"}
 
 
@@ -163,34 +195,88 @@ def run_reference(a):
     if rank != 0:
         return
     import oracle
+    if a.workload == "serving":
+        print(json.dumps({"impl": "reference", "unavailable": "serving has no oracle leg"}))
+        return
+    w = WORKLOADS[a.workload]
     threads = os.cpu_count() or 1
-    c = oracle.default_cfg(oracle.NAV, n_max=N)
-    s = oracle.reset(c, 0, [N] * E)
-    chunk = 100  # env steps per bench step: 4096 envs x 100 steps
+    n = _robots(w)
+    c = _oracle_cfg(w)
+    s = oracle.reset(c, 0, n)
+    chunk = min(100, w["T"])  # env steps per bench step: E envs x chunk steps
     for _ in range(a.warmup):
-        oracle.rollout(c, 0, s, 10, want_obs=True, threads=threads)
+        oracle.rollout(c, 0, s, min(10, chunk), want_obs=True, threads=threads)
     times = []
     for _ in range(a.steps):
         t0 = time.perf_counter()
         oracle.rollout(c, 0, s, chunk, want_obs=True, threads=threads)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
-    value = E * chunk * a.steps / tot
+    value = w["E"] * chunk * a.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_envs": E, "n_robots": N,
-                       "sample_per_step": f"{E} envs x {chunk} steps"},
+            "config": {"workload": w["desc"], "n_envs": w["E"],
+                       "sample_per_step": f"{w['E']} envs x {chunk} steps"},
             "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads,
                              "kind": "oracle",
-                             "sample": f"{E} envs x {N} robots x {chunk} steps per bench step"},
+                             "sample": f"{w['E']} envs x {chunk} steps per bench step"},
             "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(a):
+def _gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            return int(vis.split(",")[local])
+        except (ValueError, IndexError):
+            pass
+    return local
+
+
+def _teacher_forced_error(rl, w, steps=8, envs=64):
+    """Max |u* - u*_oracle| and pose error over a few teacher-forced steps on the first envs."""
+    import numpy as np
+    import torch
+
+    import oracle
+    n = _robots(w)[:envs]
+    g = rl.config_default(w["scenario"], precision=w["precision"], n_max=w["n_max"],
+                          near_frac=w["near"])
+    c = _oracle_cfg(w)
+    env = rl.Env(g, len(n), n, 0)
+    R = env.total_robots
+    us = torch.zeros(R, 2, dtype=env.dtype, device="cuda")
+    qi = torch.zeros(len(n), 4, dtype=torch.int32, device="cuda")
+    eu = ep = 0.0
+    flagged = 0
+    for _ in range(steps):
+        st = env.state_arrays()
+        s = oracle.State(c, st["n_robots"])
+        for k in ("x", "y", "th", "gx", "gy"):
+            getattr(s, k)[:] = st[k]
+        s.level[:] = st["level"]
+        s.t[:] = st["t"]
+        s.ep[:] = st["ep"]
+        s.n_res[:] = st["n_res"]
+        if st["r_max"]:
+            s.qx[:], s.qy[:] = st["qx"], st["qy"]
+            s.qlevel[:], s.qactive[:] = st["qlevel"], st["qactive"]
+        _, _, _, tr = oracle.step(c, 0, s, trace=True)
+        env.step(u_star=us, qp_info=qi)
+        st2 = env.state_arrays()
+        eu = max(eu, float(np.abs(us.cpu().numpy() - tr["u_star"]).max()))
+        ep = max(ep, float(np.abs(st2["x"] - s.x).max()), float(np.abs(st2["y"] - s.y).max()))
+        flagged += int(((qi.cpu().numpy()[:, 3] >> 1) & 1).sum())
+    env.close()
+    return {"max_control_err": eu, "max_pose_err_per_step": ep, "envs": len(n), "steps": steps,
+            "fp64_resolved": flagged}
+
+
+def run_rollout(a):
     import numpy as np
     import torch
 
@@ -205,16 +291,24 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     rl.lib()
+    w = WORKLOADS[a.workload]
+    E, T = w["E"], w["T"]
+    n = _robots(w)
     stream = torch.cuda.Stream()
-    g = rl.config_default(rl.NAVIGATION)
+    g = rl.config_default(w["scenario"], precision=w["precision"], n_max=w["n_max"],
+                          near_frac=w["near"])
+    fdt = torch.float64 if w["precision"] == 64 else torch.float32
+    esz = 8 if w["precision"] == 64 else 4
     with torch.cuda.stream(stream):
-        env = rl.Env(g, E, N, seed=1000 + rank, stream=stream)
+        env = rl.Env(g, E, n, seed=1000 + rank, stream=stream)
         rows = env.total_robots
-        obs = torch.empty(T, rows, env.obs_dim, device="cuda")
-        rew = torch.empty(T, E, device="cuda")
+        obs = torch.empty(T, rows, env.obs_dim, dtype=fdt, device="cuda")
+        rew = torch.empty(T, E, dtype=fdt, device="cuda")
         done = torch.empty(T, E, dtype=torch.uint8, device="cuda")
     stream.synchronize()
-
+    tuning = None
+    if not a.no_tune and w["precision"] == 32:
+        tuning = env.tune(min(50, T))
     for _ in range(max(3, a.warmup)):
         env.rollout(T, obs, rew, done)
     stream.synchronize()
@@ -224,14 +318,7 @@ def run_ours(a):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(a.steps)]
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except ValueError:
-            pass
-    with Clocks(gpu_index) as clk:
+    with Clocks(_gpu_index(local)) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
@@ -250,28 +337,26 @@ def run_ours(a):
         tt = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
-    env_steps = E * T * a.steps * world
-    value = env_steps / (total_ms / 1e3)
+    value = E * T * a.steps * world / (total_ms / 1e3)
 
     # ---- roofline of the rollout kernel (the only kernel of the step)
-    bytes_per_env_step = 4 * N * env.obs_dim + 4 + 1
-    state_bytes = rows * (5 * 4 * 2 + 4 * 2) + E * (4 * 2 * 2 + 8 * 4 * 2)
-    alg_bytes = E * T * bytes_per_env_step + state_bytes
+    traj_bytes = T * (rows * env.obs_dim * esz + E * esz + E)
+    state_bytes = 2 * (rows * (5 * esz + 4) + E * (3 * 4 + 8 * 4))
+    alg_bytes = traj_bytes + state_bytes
     kernel_ms = statistics.mean(per)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     peak, peak_src = _peaks()
-    traffic = _ncu_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-            "kernel": "rl::env_kernel<float, lanes, 4>",
-            "bytes_per_env_step": bytes_per_env_step}
+            "frac": achieved / peak, "traffic": _ncu_traffic(a.workload),
+            "peak_source": peak_src, "kernel": "rl::env_kernel_small / env_kernel_multi",
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "bytes_per_env_step": alg_bytes / (E * T)}
 
     extra = {}
-    # ---- plain one-launch-per-env-per-step form (bounded sample)
-    if not a.no_plain:
+    if not a.no_plain and a.workload == "nav":
         Tp = 2
-        po = torch.empty(Tp, rows, env.obs_dim, device="cuda")
-        pr = torch.empty(Tp, E, device="cuda")
+        po = torch.empty(Tp, rows, env.obs_dim, dtype=fdt, device="cuda")
+        pr = torch.empty(Tp, E, dtype=fdt, device="cuda")
         pd = torch.empty(Tp, E, dtype=torch.uint8, device="cuda")
         env.rollout(1, po, pr, pd, plain=True)
         stream.synchronize()
@@ -289,8 +374,8 @@ def run_ours(a):
     # ---- end to end through host buffers (state upload + trajectory download per step)
     blob = np.frombuffer(env.get_state(), np.uint8).copy()
     h_state = torch.from_numpy(blob).pin_memory()
-    h_obs = torch.empty(T, rows, env.obs_dim, pin_memory=True)
-    h_rew = torch.empty(T, E, pin_memory=True)
+    h_obs = torch.empty(T, rows, env.obs_dim, dtype=fdt, pin_memory=True)
+    h_rew = torch.empty(T, E, dtype=fdt, pin_memory=True)
     h_done = torch.empty(T, E, dtype=torch.uint8, pin_memory=True)
     env.rollout_host(T, h_state.numpy(), h_obs, h_rew, h_done)  # warm-up
     K2 = max(2, min(a.steps, 5))
@@ -300,43 +385,105 @@ def run_ours(a):
     e2e_s = (time.perf_counter() - t0) / K2
     e2e = {"value": E * T * world / e2e_s, "unit": "env-steps/s",
            "h2d_bytes_per_step": int(blob.nbytes),
-           "d2h_bytes_per_step": int(h_obs.numel() * 4 + h_rew.numel() * 4 + h_done.numel())}
+           "d2h_bytes_per_step": int(h_obs.numel() * esz + h_rew.numel() * esz + h_done.numel())}
 
     counters = env.counters()
+    env_steps_counted = max(1, int(counters[:, 6].sum()) * 100)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
                 "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": total_ms / a.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "scenario": "navigation", "n_envs": E,
-                           "n_robots": N, "horizon": T, "episode_len": 100,
-                           "obs": f"[{T}, {rows}, {env.obs_dim}] f32 per step",
-                           "l2": "trajectory outputs of 938 MB per step exceed the 129 MB L2",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if w["precision"] == 64 else "f32", "data": "synthetic",
+                "config": {"workload": w["desc"], "n_envs": E,
+                           "n_robots": w["N"] if w["N"] != "uneven" else "U{2..10}",
+                           "total_robots": rows, "horizon": T, "episode_len": 100,
+                           "obs": f"[{T}, {rows}, {env.obs_dim}] per step",
+                           "l2": f"trajectory outputs of {traj_bytes / 1e6:.0f} MB per step "
+                                 "(larger than the 129 MB L2 except for the tiny workload)",
                            "parallelism": f"{world} GPU(s), envs independent per rank",
-                           "lanes_per_env": env.lanes},
-                "robot_steps_per_s": value * N,
+                           "tuning": tuning},
+                "robot_steps_per_s": value * rows / E,
                 "latency_ms": {"p50": float(np.percentile(per, 50)),
                                "p99": float(np.percentile(per, 99))},
-                "roofline": roof, "e2e": e2e, "gpu_launches": a.steps,
+                "roofline": roof, "e2e": e2e,
+                "gpu_launches": a.steps,
                 "clocks": clk.summary(),
-                "qp": {"active_step_frac": float(counters[:, 3].sum()) / max(1, counters[:, 6].sum() * 100),
-                       "fp64_resolved": int(counters[:, 4].sum()),
+                "qp": {"active_step_frac": float(counters[:, 3].sum()) / env_steps_counted,
+                       "fp64_resolved_frac": float(counters[:, 4].sum()) / env_steps_counted,
                        "collisions": int(counters[:, 0].sum())}}
         line.update(extra)
+        if a.workload in ("largen", "uneven", "tiny"):
+            line["parity_sample"] = _teacher_forced_error(rl, w)
         if world == 1 and not a.no_cpu:
-            line["cpu_baseline"] = _cpu_baseline()
+            line["cpu_baseline"] = _cpu_baseline(w)
         print(json.dumps(line), flush=True)
     env.close()
     if dist:
         dist.destroy_process_group()
 
 
+def run_serving(a):
+    """Poisson arrivals (200 req/s) of rollout requests: n_envs log-uniform in [1, 2048], robots
+    uniform in {2..12}, horizon uniform in [100, 1000]; 60 GB budget; p50/p99 latency."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06771_gb300 as rl
+    from synth_inputs import serving_requests
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if rank != 0 and world > 1:
+        pass
+    g = rl.config_default(0, n_max=12)
+    srv = rl.Server(g, 60 << 30, 32)
+    reqs = serving_requests(100 + rank, a.duration, rate_hz=200.0)
+    warm = srv.submit(64, 4, 100, 1)
+    srv.drain(60.0)
+    srv.result(warm)
+    ids = []
+    with Clocks(_gpu_index(local)) as clk:
+        t0 = time.perf_counter()
+        for q in reqs:
+            dt = q["arrival_s"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(q["n_envs"], q["n_robots"], q["horizon"], q["seed"]))
+        ok = srv.drain(600.0)
+        wall = time.perf_counter() - t0
+    res = [srv.result(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["latency_s"] for r in res if r["status"] == 2]) * 1e3
+    wait = np.array([r["start_s"] - r["submit_s"] for r in res if r["status"] == 2]) * 1e3
+    env_steps = sum(r["n_envs"] * r["horizon"] for r in res if r["status"] == 2)
+    robot_steps = sum(r["n_envs"] * r["horizon"] * r["n_robots"] for r in res if r["status"] == 2)
+    line = {"metric": METRIC, "value": env_steps / wall, "unit": "env-steps/s", "n_gpus": world,
+            "steps": len(reqs), "warmup": 1, "ms_per_step": 1e3 * wall / max(1, len(reqs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson 200 req/s, n_envs log-U[1,2048], robots "
+                                   "U{2..12}, horizon U[100,1000], 60 GB budget, 32 slots",
+                       "duration_s": a.duration, "requests": len(reqs)},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean())},
+            "queue_wait_ms": {"p50": float(np.percentile(wait, 50)),
+                              "p99": float(np.percentile(wait, 99))},
+            "robot_steps_per_s": robot_steps / wall, "completed": int(len(lat)),
+            "drained": bool(ok), "peak_bytes": st["peak"], "clocks": clk.summary(),
+            "gpu_launches": len(reqs)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
-        run_ours(a)
+        run_rollout(a)
 
 
 if __name__ == "__main__":
