@@ -61,6 +61,9 @@ def _args():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form leg")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    p.add_argument("--horizon", type=int, default=0,
+                   help="override the workload's steps per rollout (small profiling cases)")
     return p.parse_args()
 
 
@@ -291,7 +294,10 @@ def run_rollout(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     rl.lib()
-    w = WORKLOADS[a.workload]
+    w = dict(WORKLOADS[a.workload])
+    if a.horizon > 0:
+        w["T"] = a.horizon
+        w["desc"] += f" (horizon overridden: {a.horizon} steps)"
     E, T = w["E"], w["T"]
     n = _robots(w)
     stream = torch.cuda.Stream()
@@ -372,20 +378,23 @@ def run_rollout(a):
         extra["speedup_vs_plain"] = value / world / pv
 
     # ---- end to end through host buffers (state upload + trajectory download per step)
-    blob = np.frombuffer(env.get_state(), np.uint8).copy()
-    h_state = torch.from_numpy(blob).pin_memory()
-    h_obs = torch.empty(T, rows, env.obs_dim, dtype=fdt, pin_memory=True)
-    h_rew = torch.empty(T, E, dtype=fdt, pin_memory=True)
-    h_done = torch.empty(T, E, dtype=torch.uint8, pin_memory=True)
-    env.rollout_host(T, h_state.numpy(), h_obs, h_rew, h_done)  # warm-up
-    K2 = max(2, min(a.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(K2):
-        env.rollout_host(T, h_state.numpy(), h_obs, h_rew, h_done)
-    e2e_s = (time.perf_counter() - t0) / K2
-    e2e = {"value": E * T * world / e2e_s, "unit": "env-steps/s",
-           "h2d_bytes_per_step": int(blob.nbytes),
-           "d2h_bytes_per_step": int(h_obs.numel() * esz + h_rew.numel() * esz + h_done.numel())}
+    e2e = None
+    if not a.no_e2e:
+        blob = np.frombuffer(env.get_state(), np.uint8).copy()
+        h_state = torch.from_numpy(blob).pin_memory()
+        h_obs = torch.empty(T, rows, env.obs_dim, dtype=fdt, pin_memory=True)
+        h_rew = torch.empty(T, E, dtype=fdt, pin_memory=True)
+        h_done = torch.empty(T, E, dtype=torch.uint8, pin_memory=True)
+        env.rollout_host(T, h_state.numpy(), h_obs, h_rew, h_done)  # warm-up
+        K2 = max(2, min(a.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(K2):
+            env.rollout_host(T, h_state.numpy(), h_obs, h_rew, h_done)
+        e2e_s = (time.perf_counter() - t0) / K2
+        e2e = {"value": E * T * world / e2e_s, "unit": "env-steps/s",
+               "h2d_bytes_per_step": int(blob.nbytes),
+               "d2h_bytes_per_step": int(h_obs.numel() * esz + h_rew.numel() * esz +
+                                         h_done.numel())}
 
     counters = env.counters()
     env_steps_counted = max(1, int(counters[:, 6].sum()) * 100)
