@@ -26,109 +26,122 @@ __device__ __forceinline__ T pick4(const T (&a)[4], int k) {
 
 constexpr int kRegRows = 4;  // active rows the register solver holds (more: shared memory)
 
-// Most violated row of the lane's own rows (circulant pair rows + its four arena rows), the q
-// active rows ak[0..q) skipped, reduced over the team: ties to the lowest row index.
-__device__ __forceinline__ void small_scan(const Team<4>& tm, int N, int P, int ndi,
-                                           const float (&Px)[4], const float (&Py)[4],
-                                           const float (&U)[8], const QPConsts<float>& c,
-                                           const int (&ak)[kRegRows], int q, float& vb, int& kb) {
-    const int i = tm.lane;
+// One barrier row: coefficient (cx, cy) on u_a and, for a pair row (b >= 0), (-cx, -cy) on u_b;
+// bound bv; key = row index * 4 + the lane that evaluates it (ties order by row index).
+struct RowD {
+    int a, b, key;
+    float cx, cy, bv;
+};
+
+__device__ __forceinline__ void own_coef(const RowD& r, int i, float& ox, float& oy) {
+    ox = (i == r.a) ? r.cx : ((i == r.b) ? -r.cx : 0.f);
+    oy = (i == r.a) ? r.cy : ((i == r.b) ? -r.cy : 0.f);
+}
+
+__device__ __forceinline__ float rowdot(const RowD& r1, const RowD& r2) {
+    return row_dot<float>(r1.a, r1.b, r1.cx, r1.cy, r2.a, r2.b, r2.cx, r2.cy);
+}
+
+__device__ __forceinline__ RowD bcast_row(const Team<4>& tm, const RowD& r, int src) {
+    RowD o;
+    o.a = __shfl_sync(tm.mask, r.a, src, 4);
+    o.b = __shfl_sync(tm.mask, r.b, src, 4);
+    o.key = __shfl_sync(tm.mask, r.key, src, 4);
+    o.cx = __shfl_sync(tm.mask, r.cx, src, 4);
+    o.cy = __shfl_sync(tm.mask, r.cy, src, 4);
+    o.bv = __shfl_sync(tm.mask, r.bv, src, 4);
+    return o;
+}
+
+// The lane's own rows for one QP: its circulant pair rows with robots jd[0] (offset 1) and
+// jd[1] (offset 2) -- key, orientation, p_a - p_b, bound -- and its four arena rows' bounds.
+struct OwnRows {
+    int pkey[2], bkey[4], pa[2];
+    float sgn[2], dx[2], dy[2], bp[2], bb[4];
+    int npair;
+};
+
+__device__ __forceinline__ void own_rows(int i, int N, int P, int ndi, const int (&jd)[2],
+                                         float px, float py, const float (&qx)[2],
+                                         const float (&qy)[2], const QPConsts<float>& c,
+                                         OwnRows& R) {
+    R.npair = (i < N) ? ndi : 0;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        const int j = jd[d];
+        const int a = min(i, j), b = max(i, j);
+        R.pa[d] = j;
+        R.pkey[d] = pair_index(a, b, N) * 4 + i;
+        R.sgn[d] = (a == i) ? 1.f : -1.f;
+        R.dx[d] = R.sgn[d] * (px - qx[d]);
+        R.dy[d] = R.sgn[d] * (py - qy[d]);
+        const float h = R.dx[d] * R.dx[d] + R.dy[d] * R.dy[d] - c.r2;
+        R.bp[d] = c.gamma * h * h * h;
+    }
+    const float bx0 = c.xmax - c.half_r - px, bx1 = px - c.xmin - c.half_r;
+    const float by0 = c.ymax - c.half_r - py, by1 = py - c.ymin - c.half_r;
+    R.bb[0] = c.kg * bx0 * bx0 * bx0;
+    R.bb[1] = c.kg * bx1 * bx1 * bx1;
+    R.bb[2] = c.kg * by0 * by0 * by0;
+    R.bb[3] = c.kg * by1 * by1 * by1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) R.bkey[s] = (P + 4 * i + s) * 4 + i;
+}
+
+// Most violated inactive row over the team at u (own ux, uy; the pair partners' nux, nuy),
+// ties to the lowest row index; the lane owning the winner broadcasts its descriptor.
+__device__ __forceinline__ void small_scan(const Team<4>& tm, int i, int N, const OwnRows& R,
+                                           float ux, float uy, const float (&nux)[2],
+                                           const float (&nuy)[2], const QPConsts<float>& c,
+                                           const int (&akey)[kRegRows], int q, float& vb,
+                                           RowD& win) {
     vb = 0.f;
-    kb = 0x7fffffff;
+    RowD best;
+    best.a = best.b = -1;
+    best.key = 0x7fffffff;
+    best.cx = best.cy = best.bv = 0.f;
     if (i < N) {
-        const float pxi = pick4(Px, i), pyi = pick4(Py, i);
-        float Ux[4], Uy[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) { Ux[m] = U[2 * m]; Uy[m] = U[2 * m + 1]; }
-        const float uxi = pick4(Ux, i), uyi = pick4(Uy, i);
-#pragma unroll
-        for (int d = 1; d <= 2; ++d) {
-            if (d <= ndi) {
-                int j = i + d;
-                if (j >= N) j -= N;
-                const int a = min(i, j), b = max(i, j);
-                const int k = pair_index(a, b, N);
-                bool act = false;
-#pragma unroll
-                for (int t = 0; t < kRegRows; ++t) act |= (t < q && ak[t] == k);
-                const float sgn = (a == i) ? 1.f : -1.f;
-                const float dx = sgn * (pxi - pick4(Px, j)), dy = sgn * (pyi - pick4(Py, j));
-                const float dux = sgn * (uxi - pick4(Ux, j)), duy = sgn * (uyi - pick4(Uy, j));
-                const float h = dx * dx + dy * dy - c.r2;
-                const float bv = c.gamma * h * h * h;
-                const float v = -2.f * (dx * dux + dy * duy) - bv;
-                if (!act && v > c.tol_abs + c.tol_rel * fabsf(bv) &&
-                    (v > vb || (v == vb && k < kb))) {
-                    vb = v;
-                    kb = k;
-                }
-            }
-        }
-        const float bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
-        const float by0 = c.ymax - c.half_r - pyi, by1 = pyi - c.ymin - c.half_r;
-        const float bvs[4] = {c.kg * bx0 * bx0 * bx0, c.kg * bx1 * bx1 * bx1,
-                              c.kg * by0 * by0 * by0, c.kg * by1 * by1 * by1};
-        const float aus[4] = {uxi, -uxi, uyi, -uyi};
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int k = P + 4 * i + s;
+        for (int d = 0; d < 2; ++d) {
             bool act = false;
 #pragma unroll
-            for (int t = 0; t < kRegRows; ++t) act |= (t < q && ak[t] == k);
-            const float v = aus[s] - bvs[s];
-            if (!act && v > c.tol_abs + c.tol_rel * fabsf(bvs[s]) &&
-                (v > vb || (v == vb && k < kb))) {
+            for (int t = 0; t < kRegRows; ++t) act |= (t < q && akey[t] == R.pkey[d]);
+            const float dux = R.sgn[d] * (ux - nux[d]), duy = R.sgn[d] * (uy - nuy[d]);
+            const float v = -2.f * (R.dx[d] * dux + R.dy[d] * duy) - R.bp[d];
+            if (d < R.npair && !act && v > c.tol_abs + c.tol_rel * fabsf(R.bp[d]) &&
+                (v > vb || (v == vb && R.pkey[d] < best.key))) {
                 vb = v;
-                kb = k;
+                best.key = R.pkey[d];
+                best.cx = -2.f * R.dx[d];
+                best.cy = -2.f * R.dy[d];
+                best.bv = R.bp[d];
+                best.a = min(i, R.pa[d]);
+                best.b = max(i, R.pa[d]);
+            }
+        }
+        const float aus[4] = {ux, -ux, uy, -uy};
+        const float cxs[4] = {1.f, -1.f, 0.f, 0.f}, cys[4] = {0.f, 0.f, 1.f, -1.f};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            bool act = false;
+#pragma unroll
+            for (int t = 0; t < kRegRows; ++t) act |= (t < q && akey[t] == R.bkey[s]);
+            const float v = aus[s] - R.bb[s];
+            if (!act && v > c.tol_abs + c.tol_rel * fabsf(R.bb[s]) &&
+                (v > vb || (v == vb && R.bkey[s] < best.key))) {
+                vb = v;
+                best.a = i; best.b = -1; best.key = R.bkey[s];
+                best.cx = cxs[s]; best.cy = cys[s]; best.bv = R.bb[s];
             }
         }
     }
+    int kb = best.key;
     tm.argmax(vb, kb);
-}
-
-// Row k as a dense coefficient vector over u = [u_0x, u_0y, ..., u_3x, u_3y], its bound b and,
-// for a pair row, h = |p_a - p_b|^2 - r^2 (arena rows: h = +inf).
-__device__ __forceinline__ void small_row(int k, int N, int P, const float (&Px)[4],
-                                          const float (&Py)[4], const QPConsts<float>& c,
-                                          float (&a)[8], float& b, float& h) {
-    int ia, ib;
-    float ax, ay;
-    if (k < P) {
-        int pa, pb;
-        pair_of(k, N, pa, pb);
-        const float dx = pick4(Px, pa) - pick4(Px, pb), dy = pick4(Py, pa) - pick4(Py, pb);
-        h = dx * dx + dy * dy - c.r2;
-        ia = pa;
-        ib = pb;
-        ax = -2.f * dx;
-        ay = -2.f * dy;
-        b = c.gamma * h * h * h;
-    } else {
-        const int r = k - P;
-        ia = r >> 2;
-        ib = -1;
-        const int s = r & 3;
-        const float pxi = pick4(Px, ia), pyi = pick4(Py, ia);
-        float d;
-        if (s == 0) { ax = 1.f; ay = 0.f; d = c.xmax - c.half_r - pxi; }
-        else if (s == 1) { ax = -1.f; ay = 0.f; d = pxi - c.xmin - c.half_r; }
-        else if (s == 2) { ax = 0.f; ay = 1.f; d = c.ymax - c.half_r - pyi; }
-        else { ax = 0.f; ay = -1.f; d = pyi - c.ymin - c.half_r; }
-        b = c.kg * d * d * d;
-        h = CUDART_INF_F;
+    if (kb == 0x7fffffff) {
+        win.key = kb;
+        return;
     }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        a[2 * m] = (m == ia) ? ax : ((m == ib) ? -ax : 0.f);
-        a[2 * m + 1] = (m == ia) ? ay : ((m == ib) ? -ay : 0.f);
-    }
-}
-
-__device__ __forceinline__ float dot8(const float (&a)[8], const float (&b)[8]) {
-    float s = 0.f;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) s += a[m] * b[m];
-    return s;
+    win = bcast_row(tm, best, kb & 3);
 }
 
 __device__ __forceinline__ int ltri(int i, int k) { return i * (i + 1) / 2 + k; }
@@ -150,14 +163,15 @@ static __device__ __noinline__ QPResult small_general(const Team<4> tm, TeamSmem
     return qp_solve<float, 4, 4>(tm, W, N, c);  // the minimiser is left in W.ux / W.uy
 }
 
-// The barrier QP of one env of N <= 4 robots, filtered velocity of the lane's own robot.
-// The dual active-set method runs in registers on dense 8-vectors with up to kRegRows active
-// rows; every lane of the team computes the same iterates.  The common cases cost one scan (no
-// active row) or one closed-form half-plane projection and a confirming scan (one active row).
-// An active set larger than kRegRows goes to the shared-memory solver.
+// The barrier QP of one env of N <= 4 robots; (usx, usy) receives the lane's own robot's
+// filtered velocity.  The dual active-set method runs with u distributed over the lanes (lane i
+// holds u_i), the active rows' descriptors, multipliers and Cholesky factor replicated in
+// registers (at most kRegRows rows), dot products over u as team sums.  The first iteration is
+// the closed-form projection onto the first row's half-plane: its violation is the scan's
+// maximum and |a|^2 is known.  A larger active set goes to the shared-memory solver.
 __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<float, 4>& S, int N,
-                                                 const float (&Px)[4], const float (&Py)[4],
-                                                 const float (&U0x)[4], const float (&U0y)[4],
+                                                 const int (&jd)[2], int ndi, float px,
+                                                 float py, float u0x, float u0y,
                                                  const QPConsts<float>& c, float& usx,
                                                  float& usy) {
     QPResult res;
@@ -167,60 +181,68 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
     res.flag = false;
     const int i = tm.lane;
     const int P = N * (N - 1) / 2;
-    const int nd = (N - 1) / 2;
-    const int ndi = (i < N) ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
-    float U[8];
+    float qx[2], qy[2], nux[2], nuy[2];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        U[2 * m] = U0x[m];
-        U[2 * m + 1] = U0y[m];
+    for (int d = 0; d < 2; ++d) {
+        qx[d] = __shfl_sync(tm.mask, px, jd[d], 4);
+        qy[d] = __shfl_sync(tm.mask, py, jd[d], 4);
+        nux[d] = __shfl_sync(tm.mask, u0x, jd[d], 4);
+        nuy[d] = __shfl_sync(tm.mask, u0y, jd[d], 4);
     }
-    int ak[kRegRows];
-    float AR[kRegRows][8], lam[kRegRows], ah[kRegRows];
-    float L[kRegRows * (kRegRows + 1) / 2], dinv[kRegRows];
+    OwnRows R;
+    own_rows(i, N, P, ndi, jd, px, py, qx, qy, c, R);
+    float ux = u0x, uy = u0y;
+    int akey[kRegRows];
 #pragma unroll
-    for (int t = 0; t < kRegRows; ++t) ak[t] = -1;
-    int q = 0;
+    for (int t = 0; t < kRegRows; ++t) akey[t] = -1;
     float vb;
-    int kb;
-    small_scan(tm, N, P, ndi, Px, Py, U, c, ak, 0, vb, kb);
-    if (kb != 0x7fffffff) {
-        // first iteration in closed form: the projection onto the half-plane of row kb
-        float ap[8], bp, hp;
-        small_row(kb, N, P, Px, Py, c, ap, bp, hp);
-        const float app = dot8(ap, ap);
-        const float st = (dot8(ap, U) - bp) / app;
+    RowD p;
+    small_scan(tm, i, N, R, ux, uy, nux, nuy, c, akey, 0, vb, p);
+    usx = ux;
+    usy = uy;
+    if (p.key == 0x7fffffff) return res;
+
+    // first iteration, closed form: u <- u - (v / |a|^2) a
+    RowD A[kRegRows];
+    float lam[kRegRows], L[kRegRows * (kRegRows + 1) / 2], dinv[kRegRows];
+    {
+        const float app = (p.b >= 0 ? 2.f : 1.f) * (p.cx * p.cx + p.cy * p.cy);
+        const float st = vb / app;
+        float ox, oy;
+        own_coef(p, i, ox, oy);
+        ux -= st * ox;
+        uy -= st * oy;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            U[m] -= st * ap[m];
-            AR[0][m] = ap[m];
+        for (int d = 0; d < 2; ++d) {  // the partners' u change the same way: no re-fetch
+            own_coef(p, jd[d], ox, oy);
+            nux[d] -= st * ox;
+            nuy[d] -= st * oy;
         }
-        const float dg = sqrtf(app);
-        L[0] = dg;
-        dinv[0] = 1.f / dg;
-        ak[0] = kb;
+        A[0] = p;
+        akey[0] = p.key;
         lam[0] = st;
-        ah[0] = hp;
-        q = 1;
-        res.iters = 1;
-        small_scan(tm, N, P, ndi, Px, Py, U, c, ak, 1, vb, kb);
+        L[0] = sqrtf(app);
+        dinv[0] = 1.f / L[0];
     }
+    int q = 1;
+    res.iters = 1;
+    small_scan(tm, i, N, R, ux, uy, nux, nuy, c, akey, q, vb, p);
     bool overflow = false;
-    while (kb != 0x7fffffff) {
+    while (p.key != 0x7fffffff) {
         if (++res.iters > c.max_iter) { res.status = 2; break; }
-        float ap[8], bp, hp;
-        small_row(kb, N, P, Px, Py, c, ap, bp, hp);
-        const float app = dot8(ap, ap);
+        const float app = (p.b >= 0 ? 2.f : 1.f) * (p.cx * p.cx + p.cy * p.cy);
+        float pox, poy;
+        own_coef(p, i, pox, poy);
         float lam_p = 0.f;
         bool added = false;
         for (int guard = 0; guard <= kRegRows + 1 && !added; ++guard) {
-            // r = G^-1 N^T a_p (forward and back substitution), z = a_p - N r
+            // r = G^-1 N^T a_p, z = a_p - N r (own robot's two components)
             float y[kRegRows], r[kRegRows];
 #pragma unroll
             for (int t = 0; t < kRegRows; ++t) {
                 y[t] = 0.f;
                 if (t < q) {
-                    float s = dot8(AR[t], ap);
+                    float s = rowdot(A[t], p);
 #pragma unroll
                     for (int m = 0; m < t; ++m) s -= L[ltri(t, m)] * y[m];
                     y[t] = s * dinv[t];
@@ -237,16 +259,16 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
                     r[t] = s * dinv[t];
                 }
             }
-            float z[8];
-#pragma unroll
-            for (int m = 0; m < 8; ++m) z[m] = ap[m];
+            float zx = pox, zy = poy;
 #pragma unroll
             for (int t = 0; t < kRegRows; ++t)
                 if (t < q) {
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) z[m] -= r[t] * AR[t][m];
+                    float ox, oy;
+                    own_coef(A[t], i, ox, oy);
+                    zx -= r[t] * ox;
+                    zy -= r[t] * oy;
                 }
-            const float zz = dot8(z, z);
+            const float zz = tm.sum(zx * zx + zy * zy);
             float td = CUDART_INF_F;
             int jb = -1;
 #pragma unroll
@@ -255,7 +277,7 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
                     const float tj = lam[t] / r[t];
                     if (tj < td) { td = tj; jb = t; }
                 }
-            const float sp = dot8(ap, U) - bp;
+            const float sp = tm.sum(pox * ux + poy * uy) - p.bv;
             const bool indep = zz > c.eps_dep * app;
             if (!indep) res.flag = true;
             const float tf = indep ? sp / zz : CUDART_INF_F;
@@ -265,8 +287,8 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
             }
             const float st = tf < td ? tf : td;
             if (tf < CUDART_INF_F) {
-#pragma unroll
-                for (int m = 0; m < 8; ++m) U[m] -= st * z[m];
+                ux -= st * zx;
+                uy -= st * zy;
             }
 #pragma unroll
             for (int t = 0; t < kRegRows; ++t)
@@ -282,11 +304,9 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
                         for (int m = 0; m < t; ++m) L[ltri(t, m)] = y[m];
                         L[ltri(t, t)] = dg;
                         dinv[t] = 1.f / dg;
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) AR[t][m] = ap[m];
-                        ak[t] = kb;
+                        A[t] = p;
+                        akey[t] = p.key;
                         lam[t] = lam_p;
-                        ah[t] = hp;
                     }
                 }
                 ++q;
@@ -296,21 +316,21 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
 #pragma unroll
                 for (int t = 0; t < kRegRows - 1; ++t)
                     if (t >= jb) {
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) AR[t][m] = AR[t + 1][m];
-                        ak[t] = ak[t + 1];
+                        A[t] = A[t + 1];
+                        akey[t] = akey[t + 1];
                         lam[t] = lam[t + 1];
-                        ah[t] = ah[t + 1];
                     }
                 --q;
-                ak[q] = -1;
+#pragma unroll
+                for (int t = 0; t < kRegRows; ++t)
+                    if (t >= q) akey[t] = -1;
                 bool ok = true;
 #pragma unroll
                 for (int t = 0; t < kRegRows; ++t)
                     if (t < q) {
 #pragma unroll
                         for (int m = 0; m <= t; ++m) {
-                            float g = dot8(AR[t], AR[m]);
+                            float g = rowdot(A[t], A[m]);
 #pragma unroll
                             for (int n = 0; n < m; ++n) g -= L[ltri(t, n)] * L[ltri(m, n)];
                             if (m == t) {
@@ -328,10 +348,15 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
         }
         if (res.status != 0 || overflow) break;
         if (!added) { res.status = 2; break; }
-        small_scan(tm, N, P, ndi, Px, Py, U, c, ak, q, vb, kb);
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            nux[d] = __shfl_sync(tm.mask, ux, jd[d], 4);
+            nuy[d] = __shfl_sync(tm.mask, uy, jd[d], 4);
+        }
+        small_scan(tm, i, N, R, ux, uy, nux, nuy, c, akey, q, vb, p);
     }
     if (overflow) {
-        res = small_general(tm, S, N, pick4(Px, i), pick4(Py, i), pick4(U0x, i), pick4(U0y, i), c);
+        res = small_general(tm, S, N, px, py, u0x, u0y, c);
         usx = (i < N) ? S.qp.f.ux[i] : 0.f;
         usy = (i < N) ? S.qp.f.uy[i] : 0.f;
         tm.sync();
@@ -341,19 +366,15 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
     if (res.status == 0) {
 #pragma unroll
         for (int t = 0; t < kRegRows; ++t)
-            if (t < q && ah[t] < c.h_flag) res.flag = true;  // near-degenerate pair row
+            if (t < q && A[t].b >= 0 &&
+                0.25f * (A[t].cx * A[t].cx + A[t].cy * A[t].cy) - c.r2 < c.h_flag)
+                res.flag = true;  // near-degenerate pair row
     } else {
         res.flag = true;
-        if (res.status == 1) {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) U[m] = 0.f;
-        }
+        if (res.status == 1) { ux = 0.f; uy = 0.f; }
     }
-    float Ux[4], Uy[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) { Ux[m] = U[2 * m]; Uy[m] = U[2 * m + 1]; }
-    usx = pick4(Ux, i);
-    usy = pick4(Uy, i);
+    usx = ux;
+    usy = uy;
     return res;
 }
 
@@ -511,8 +532,17 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     tm.sync();
     const int nd = (N - 1) / 2;
     const int ndi = own ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
+    int jn[2];  // the robots of the lane's circulant pair rows (offsets 1 and 2)
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        int j = i + d + 1;
+        while (j >= N) j -= N;
+        jn[d] = own ? j : i;
+    }
     const float* acts = actions;
     float ret_acc = 0.f;
+    int nz_t = -2, nz_ep = -1;   // noise words cached for step nz_t + 1 of episode nz_ep
+    uint32_t nz_nx = 0u, nz_ny = 0u;
 
     for (int step = 0; step < A.T; ++step) {
         // ---- projected point and nominal SI velocity of the own robot
@@ -527,8 +557,27 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
             ux = k.k_si * (tx - px);
             uy = k.k_si * (ty - py);
             cap_fast(ux, uy, k.vmax);
-            const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)t);
-            const uint32_t wx = (i & 1) ? w.w[2] : w.w[0], wy = (i & 1) ? w.w[3] : w.w[1];
+            // Noise words of this robot for step t.  Robots 2m and 2m+1 share the Philox block
+            // (pair m, step t); their two lanes compute the blocks of steps t and t+1 at once
+            // and swap them, so each lane runs Philox every other step.
+            uint32_t wx, wy;
+            if (nz_ep == ep && nz_t + 1 == t) {
+                wx = nz_nx;
+                wy = nz_ny;
+                nz_t = -2;
+            } else {
+                const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)(t + (i & 1)));
+                uint32_t o[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) o[m] = __shfl_xor_sync(tm.mask, w.w[m], 1, 4);
+                // block of step t: the even lane's; of step t+1: the odd lane's
+                wx = (i & 1) ? o[2] : w.w[0];
+                wy = (i & 1) ? o[3] : w.w[1];
+                nz_nx = (i & 1) ? w.w[2] : o[0];
+                nz_ny = (i & 1) ? w.w[3] : o[1];
+                nz_t = t;
+                nz_ep = ep;
+            }
             const float ex = __fmul_rn(__fsub_rn(unit24(wx), 0.5f), k.noise_scale);
             const float ey = __fmul_rn(__fsub_rn(unit24(wy), 0.5f), k.noise_scale);
             ux += k.noise_on ? ex : 0.f;
@@ -536,17 +585,9 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         }
         cap_fast(ux, uy, k.vmax);
         const float dold = fast_norm(px - gx, py - gy);
-        // ---- all-gather and the barrier QP
-        float Px[4], Py[4], U0x[4], U0y[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            Px[r] = __shfl_sync(tm.mask, px, r, 4);
-            Py[r] = __shfl_sync(tm.mask, py, r, 4);
-            U0x[r] = __shfl_sync(tm.mask, ux, r, 4);
-            U0y[r] = __shfl_sync(tm.mask, uy, r, 4);
-        }
+        // ---- the barrier QP
         float usx, usy;
-        QPResult res = small_filter(tm, S, N, Px, Py, U0x, U0y, qc, usx, usy);
+        QPResult res = small_filter(tm, S, N, jn, ndi, px, py, ux, uy, qc, usx, usy);
         int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
         if (k.resolve_f64 && res.flag) {
             const QPResult r64 = small_resolve_f64(tm, S, k, N, x, y, th, ux, uy);
@@ -576,19 +617,13 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         __sincosf(th, &sn, &cs);
         const float npx = x + k.l * cs, npy = y + k.l * sn;
         // ---- flags, reward, scenario transition
-        float Qx[4], Qy[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            Qx[r] = __shfl_sync(tm.mask, npx, r, 4);
-            Qy[r] = __shfl_sync(tm.mask, npy, r, 4);
-        }
         int flags_l = 0;  // collisions in the low half, out-of-arena in the high half
 #pragma unroll
-        for (int d = 1; d <= 2; ++d) {
-            int j = i + d;
-            j = (j >= N) ? j - N : j;
-            const float dx = npx - pick4(Qx, j), dy = npy - pick4(Qy, j);
-            flags_l += (d <= ndi && dx * dx + dy * dy < k.r2) ? 1 : 0;
+        for (int d = 0; d < 2; ++d) {
+            const float qx = __shfl_sync(tm.mask, npx, jn[d], 4);
+            const float qy = __shfl_sync(tm.mask, npy, jn[d], 4);
+            const float dx = npx - qx, dy = npy - qy;
+            flags_l += (d < ndi && dx * dx + dy * dy < k.r2) ? 1 : 0;
         }
         flags_l += (own && (npx < k.xmin || npx > k.xmax || npy < k.ymin || npy > k.ymax)) ? 65536 : 0;
         float rew_l = (!forage && own) ? dold - fast_norm(npx - gx, npy - gy) : 0.f;
@@ -650,13 +685,6 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         }
         // ---- observations of the own robot
         if (A.io.obs) {
-            float X[4], Y[4], TH[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                X[r] = __shfl_sync(tm.mask, x, r, 4);
-                Y[r] = __shfl_sync(tm.mask, y, r, 4);
-                TH[r] = __shfl_sync(tm.mask, th, r, 4);
-            }
             const int od = A.io.obs_dim;
             float* o = A.io.obs + (long long)step * A.io.obs_step + (long long)row * od;
             if (!forage) {
@@ -666,9 +694,12 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
                 for (int sl = 0; sl < 3; ++sl) {
                     const int j = sl + (sl >= i ? 1 : 0);
                     const bool live = j < N;
-                    rel[3 * sl] = live ? pick4(X, j) - x : 0.f;
-                    rel[3 * sl + 1] = live ? pick4(Y, j) - y : 0.f;
-                    rel[3 * sl + 2] = live ? wrap_pi_f(pick4(TH, j) - th) : 0.f;
+                    const float xj = __shfl_sync(tm.mask, x, j, 4);
+                    const float yj = __shfl_sync(tm.mask, y, j, 4);
+                    const float tj = __shfl_sync(tm.mask, th, j, 4);
+                    rel[3 * sl] = live ? xj - x : 0.f;
+                    rel[3 * sl + 1] = live ? yj - y : 0.f;
+                    rel[3 * sl + 2] = live ? wrap_pi_f(tj - th) : 0.f;
                 }
                 if (own) {
                     if (od == 14) {
@@ -692,9 +723,15 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
                     }
                 }
             } else {
+                float X[4], Y[4], TH[4];
                 int LV[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) LV[r] = __shfl_sync(tm.mask, lv, r, 4);
+                for (int r = 0; r < 4; ++r) {
+                    X[r] = __shfl_sync(tm.mask, x, r, 4);
+                    Y[r] = __shfl_sync(tm.mask, y, r, 4);
+                    TH[r] = __shfl_sync(tm.mask, th, r, 4);
+                    LV[r] = __shfl_sync(tm.mask, lv, r, 4);
+                }
                 if (own) small_forage_obs(S, k, o, i, N, n_res, x, y, th, lv, X, Y, TH, LV);
             }
         }
@@ -728,15 +765,21 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     }
 }
 
+// A.warp_envs teams (envs) per 32-lane warp, 1..8 (0: 4); with fewer than 8 the other lanes
+// idle, which trades SIMD width for less divergence between envs and more warps per scheduler
+// (4 per warp measured fastest for 4096 envs of 4 robots).
 template <bool FAST>
 __global__ void __launch_bounds__(128, 1) env_kernel_small(LaunchArgs<float> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Team<4> tm;
-    const int teams_per_block = blockDim.x / 4;
+    const int per = (A.warp_envs >= 1 && A.warp_envs <= 8) ? A.warp_envs : 4;
+    const int tiw = (threadIdx.x & 31) >> 2;  // team in warp
+    if (tiw >= per) return;
     const int tib = threadIdx.x / 4;
     TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + tib;
-    const int total_teams = gridDim.x * teams_per_block;
-    for (int idx = blockIdx.x * teams_per_block + tib; idx < A.n_list; idx += total_teams) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int idx = warp * per + tiw; idx < A.n_list; idx += warps * per) {
         const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
         run_env_small<FAST>(A, tm, *S, e);
     }

@@ -89,6 +89,7 @@ struct LaunchArgs {
     int n_list;
     int env_begin;
     int T;
+    int warp_envs;  // one-thread-per-env kernel: envs per 32-lane warp
     uint64_t seed;
 };
 

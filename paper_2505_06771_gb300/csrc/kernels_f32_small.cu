@@ -1,9 +1,13 @@
-// Binary32 kernels of the 4-robot class: the register-resident team kernel (4 lanes per env)
-// and the generic shared-memory kernel with 1 or 2 lanes per env (tuner candidates).
+// Binary32 kernels of the 4-robot class: one thread per env (Navigation, scripted, no traces),
+// the register-resident team kernel (4 lanes per env), and the generic shared-memory kernel with
+// 2 lanes per env (a tuner candidate).
 #include "env_small.cuh"
+#include "env_thread.cuh"
 #include "launch.h"
 
 namespace rl {
+
+static bool is_fast(const LaunchArgs<float>& a);
 
 static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threads,
                                      int max_blocks, cudaStream_t st) {
@@ -11,25 +15,47 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     if (block_threads > 128) block_threads = 128;  // the kernel's launch bound
     const int tpb = block_threads / 4;
     const size_t smem = (size_t)tpb * sizeof(TeamSmem<float, 4>);
-    const bool fast = a.k.scenario == 0 && a.io.actions == nullptr && a.io.u_nom == nullptr &&
-                      a.io.u_star == nullptr && a.io.vw == nullptr && a.io.qp_info == nullptr;
+    const bool fast = is_fast(a);
+    const int per = (a.warp_envs >= 1 && a.warp_envs <= 8) ? a.warp_envs : 4;
     void (*kern)(LaunchArgs<float>) = fast ? env_kernel_small<true> : env_kernel_small<false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    int blocks = (a.n_list + tpb - 1) / tpb;
+    const int envs_per_block = (block_threads / 32) * per;
+    int blocks = (a.n_list + envs_per_block - 1) / envs_per_block;
     if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     if (blocks <= 0) return cudaSuccess;
     kern<<<blocks, block_threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+// One thread per env: block_threads / 4 envs per warp (8, 16 or 32), one warp per block.
+static cudaError_t launch_thread(const LaunchArgs<float>& a, int block_threads, int max_blocks,
+                                 cudaStream_t st) {
+    LaunchArgs<float> b = a;
+    b.warp_envs = std::min(32, std::max(1, block_threads / 4));
+    int blocks = (a.n_list + b.warp_envs - 1) / b.warp_envs;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+    if (blocks <= 0) return cudaSuccess;
+    env_kernel_thread<<<blocks, 32, 32 * sizeof(QPWork<double, 4>), st>>>(b);
+    return cudaGetLastError();
+}
+
+static bool is_fast(const LaunchArgs<float>& a) {
+    return a.k.scenario == 0 && a.io.actions == nullptr && a.io.u_nom == nullptr &&
+           a.io.u_star == nullptr && a.io.vw == nullptr && a.io.qp_info == nullptr;
+}
+
 cudaError_t launch_f32_small(const LaunchArgs<float>& a, int lanes, int block_threads,
                              int max_blocks, cudaStream_t st, bool reset) {
     switch (lanes) {
-        case 1: return launch_one<float, 1, 4>(a, block_threads, max_blocks, st, reset);
+        case 1:
+            // Navigation, scripted, no traces: one thread per env; otherwise the 4-lane team
+            if (reset) return launch_one<float, 4, 4>(a, 64, max_blocks, st, true);
+            if (is_fast(a)) return launch_thread(a, block_threads, max_blocks, st);
+            return launch_small_regs(a, 64, max_blocks, st);
         case 2: return launch_one<float, 2, 4>(a, block_threads, max_blocks, st, reset);
         case 4:
             if (reset) return launch_one<float, 4, 4>(a, block_threads, max_blocks, st, true);

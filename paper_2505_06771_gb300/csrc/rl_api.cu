@@ -35,6 +35,7 @@ static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
 
 struct Class {
     int nmax, lanes, begin, count, block_threads;
+    int warp_envs;  // envs per warp for the 4-robot binary32 kernels (0: full warps)
 };
 
 }  // namespace
@@ -153,6 +154,7 @@ cudaError_t launch_class(const rl_env* h, const Class& c, rl::LaunchArgs<R> a, b
                          int max_blocks = 0) {
     a.env_list = h->d_lists + c.begin;
     a.n_list = c.count;
+    a.warp_envs = c.warp_envs;
     if constexpr (std::is_same<R, double>::value) {
         return rl::launch_f64(a, c.nmax, c.lanes, c.block_threads, max_blocks, h->st, reset);
     } else {
@@ -289,6 +291,7 @@ rl_status rl_config_default(int32_t scenario, rl_config* out) {
     out->resolve_f64 = 1;
     out->lanes = 0;
     out->block_threads = 0;
+    out->warp_envs = 0;
     out->gamma = 100.0;
     out->r = 0.17;
     out->l = 0.05;
@@ -385,6 +388,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         if (!(lanes > 0 && (ok & (unsigned)lanes))) lanes = nm;
         k.lanes = lanes;
         k.block_threads = nm <= 8 ? 64 : (nm == 16 ? 64 : 32);
+        k.warp_envs = cfg->warp_envs > 0 ? std::min(32, cfg->warp_envs) : 0;
         if (cfg->block_threads > 0) {
             if (cfg->block_threads % 32 != 0 || cfg->block_threads > 256) { rl_destroy(h); return RL_ERR_ARG; }
             k.block_threads = std::max(cfg->block_threads, lanes);
@@ -561,16 +565,28 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
         const unsigned ok = rl::supported_lanes(h->prec, all[c].nmax);
         float best = 1e30f;
         Class pick = all[c];
-        for (int lanes = 1; lanes <= 32 && st == RL_OK; lanes <<= 1) {
-            if (!(ok & (unsigned)lanes)) continue;
-            for (int b = 0; b < 3 && st == RL_OK; ++b) {
-                if (bts[b] < lanes) continue;
-                h->cls[0].lanes = lanes;
-                h->cls[0].block_threads = bts[b];
-                float ms = 0.f;
-                st = probe(ms);
-                if (st == RL_OK && ms < best) { best = ms; pick = h->cls[0]; }
+        // candidates (lanes, block threads, envs per warp)
+        int cand[16][3];
+        int nc_ = 0;
+        if (h->prec == 32 && all[c].nmax == 4) {
+            const int we4[4] = {1, 2, 4, 8}, we1[3] = {8, 16, 32};
+            for (int w = 0; w < 4; ++w) { cand[nc_][0] = 4; cand[nc_][1] = 128; cand[nc_][2] = we4[w]; ++nc_; }
+            for (int w = 0; w < 3; ++w) { cand[nc_][0] = 1; cand[nc_][1] = 4 * we1[w]; cand[nc_][2] = 0; ++nc_; }
+            cand[nc_][0] = 2; cand[nc_][1] = 64; cand[nc_][2] = 0; ++nc_;
+        } else {
+            for (int lanes = 1; lanes <= 32; lanes <<= 1) {
+                if (!(ok & (unsigned)lanes)) continue;
+                for (int b = 0; b < 3; ++b)
+                    if (bts[b] >= lanes) { cand[nc_][0] = lanes; cand[nc_][1] = bts[b]; cand[nc_][2] = 0; ++nc_; }
             }
+        }
+        for (int ci = 0; ci < nc_ && st == RL_OK; ++ci) {
+            h->cls[0].lanes = cand[ci][0];
+            h->cls[0].block_threads = cand[ci][1];
+            h->cls[0].warp_envs = cand[ci][2];
+            float ms = 0.f;
+            st = probe(ms);
+            if (st == RL_OK && ms < best) { best = ms; pick = h->cls[0]; }
         }
         for (int i = 0; i < nc; ++i) h->cls[i] = all[i];
         h->ncls = nc;
@@ -600,9 +616,10 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     if (h_choice) {
         h_choice[0] = h->use_multi;
         for (int c = 0; c < 4; ++c) {
-            h_choice[1 + 3 * c] = c < h->ncls ? h->cls[c].nmax : 0;
-            h_choice[2 + 3 * c] = c < h->ncls ? h->cls[c].lanes : 0;
-            h_choice[3 + 3 * c] = c < h->ncls ? h->cls[c].block_threads : 0;
+            h_choice[1 + 4 * c] = c < h->ncls ? h->cls[c].nmax : 0;
+            h_choice[2 + 4 * c] = c < h->ncls ? h->cls[c].lanes : 0;
+            h_choice[3 + 4 * c] = c < h->ncls ? h->cls[c].block_threads : 0;
+            h_choice[4 + 4 * c] = c < h->ncls ? h->cls[c].warp_envs : 0;
         }
     }
     return RL_OK;

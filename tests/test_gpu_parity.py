@@ -76,9 +76,14 @@ def test_reset_sampler_bit_exact(rl, prec, case):
     env.close()
 
 
-def _teacher_forced(rl, g, o, n, seed, steps, actions=False):
+def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
+    """Both sides step from the same state.  traces=False calls the step with observations,
+    rewards and done flags only, which selects the one-thread-per-env Navigation kernel."""
     env = rl.Env(g, len(n), n, seed)
     b = _alloc(env)
+    if not traces:
+        for k in ("u_nom", "u_star", "vw", "qp_info"):
+            b[k] = None
     err = dict(u_nom=0.0, u_star=0.0, v=0.0, w=0.0, pose=0.0, th=0.0, rew=0.0, obs=0.0)
     rng = np.random.default_rng(seed)
     flagged = 0
@@ -97,11 +102,13 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False):
         st2 = env.state_arrays()
         done_g = b["done"].cpu().numpy()
         assert np.array_equal(done_g, done_o), f"done differs at step {t}"
-        err["u_nom"] = max(err["u_nom"], np.abs(b["u_nom"].cpu().numpy() - tr["u_nom"]).max())
-        err["u_star"] = max(err["u_star"], np.abs(b["u_star"].cpu().numpy() - tr["u_star"]).max())
-        vw = b["vw"].cpu().numpy()
-        err["v"] = max(err["v"], np.abs(vw[:, 0] - tr["vw"][:, 0]).max())
-        err["w"] = max(err["w"], np.abs(vw[:, 1] - tr["vw"][:, 1]).max())
+        if traces:
+            err["u_nom"] = max(err["u_nom"], np.abs(b["u_nom"].cpu().numpy() - tr["u_nom"]).max())
+            err["u_star"] = max(err["u_star"],
+                                np.abs(b["u_star"].cpu().numpy() - tr["u_star"]).max())
+            vw = b["vw"].cpu().numpy()
+            err["v"] = max(err["v"], np.abs(vw[:, 0] - tr["vw"][:, 0]).max())
+            err["w"] = max(err["w"], np.abs(vw[:, 1] - tr["vw"][:, 1]).max())
         err["pose"] = max(err["pose"], np.abs(st2["x"] - s.x).max(), np.abs(st2["y"] - s.y).max())
         err["th"] = max(err["th"], np.abs(wrap(st2["th"] - s.th)).max())
         err["rew"] = max(err["rew"], np.abs(b["reward"].cpu().numpy() - rew_o).max())
@@ -114,8 +121,9 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False):
         cg, co = st2["counters"], s.counters.reshape(-1, 8)
         for c in (0, 1, 2, 6):
             assert np.array_equal(cg[:, c], co[:, c]), f"counter {c} differs at step {t}"
-        qi = b["qp_info"].cpu().numpy()
-        flagged += int(((qi[:, 3] >> 1) & 1).sum())
+        if traces:
+            qi = b["qp_info"].cpu().numpy()
+            flagged += int(((qi[:, 3] >> 1) & 1).sum())
     env.close()
     return err, flagged
 
@@ -145,6 +153,19 @@ def test_teacher_forced_binary32(rl, case):
     assert err["u_star"] < U_TOL
     assert err["v"] < U_TOL and err["w"] < U_TOL / g["l"]
     assert err["pose"] < 1e-6 and err["th"] < 1e-5
+    assert err["rew"] < 1e-5 and err["obs"] < 1e-5
+
+
+@pytest.mark.parametrize("N,E", [(4, 600), (3, 300), (2, 200)])
+def test_teacher_forced_thread_kernel(rl, N, E):
+    """The one-thread-per-env kernel (Navigation, scripted, no traces): poses, observations and
+    rewards against the oracle stepped from the same state.  A pose error within 1e-6 per step
+    bounds the filtered-control error by about 1e-6 / dt = 3e-5 and checks that every step used
+    the same barrier QP solution (an active-set mistake moves a robot by ~1e-4 m per step)."""
+    g, o = make_pair(0, N, episode_len=30)
+    err, _ = _teacher_forced(rl, g, o, [N] * E, 91, 40, traces=False)
+    print(f"\nthread kernel N={N}: max errors {err}")
+    assert err["pose"] < 1e-6 and err["th"] < 2e-5
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
 
