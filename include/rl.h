@@ -156,8 +156,8 @@ rl_status rl_rollout_plain(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew
    state, restored afterwards) for every launch shape -- lanes per environment and threads per
    block for each robot-count class, and for an uneven batch one persistent launch over all
    classes against one launch per class -- and keeps the fastest for later rollouts.
-   h_choice (NULL or 17 ints): [one-launch flag, then per class (nmax, lanes, block threads,
-   envs per warp)].
+   h_choice (NULL or 21 ints): [one-launch flag, then per robot-count class (nmax, lanes,
+   block threads, envs per warp)].
    Synchronises the stream.  RL_ERR_STATE if the handle is not scripted. */
 rl_status rl_tune(rl_env* env, int32_t T_probe, int32_t* h_choice);
 

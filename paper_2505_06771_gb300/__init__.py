@@ -258,14 +258,14 @@ class Env:
 
     def tune(self, T_probe: int = 50) -> dict:
         """rl_tune: pick the fastest launch shape for this batch; returns the choice."""
-        out = np.zeros(17, np.int32)
+        out = np.zeros(21, np.int32)
         self._check(self._L.rl_tune(self._h, T_probe, out.ctypes.data), "rl_tune")
         self.lanes = int(self._L.rl_lanes(self._h))
         return {"one_launch": bool(out[0]),
                 "classes": [dict(nmax=int(out[1 + 4 * c]), lanes=int(out[2 + 4 * c]),
                                  block_threads=int(out[3 + 4 * c]),
                                  warp_envs=int(out[4 + 4 * c]))
-                            for c in range(4) if out[1 + 4 * c] > 0]}
+                            for c in range(5) if out[1 + 4 * c] > 0]}
 
     def state_bytes(self) -> int:
         return int(self._L.rl_state_bytes(self._h))

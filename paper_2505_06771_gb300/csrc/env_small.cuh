@@ -151,7 +151,7 @@ __device__ __forceinline__ int ltri(int i, int k) { return i * (i + 1) / 2 + k; 
 static __device__ __noinline__ QPResult small_general(const Team<4> tm, TeamSmem<float, 4>& S, int N,
                                                float px, float py, float u0x, float u0y,
                                                const QPConsts<float> c) {
-    QPWork<float, 4>& W = S.qp.f;
+    QPWork<float, 4>& W = S.qp.s.f;
     const int i = tm.lane;
     if (i < N) {
         W.px[i] = px;
@@ -357,8 +357,8 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
     }
     if (overflow) {
         res = small_general(tm, S, N, px, py, u0x, u0y, c);
-        usx = (i < N) ? S.qp.f.ux[i] : 0.f;
-        usy = (i < N) ? S.qp.f.uy[i] : 0.f;
+        usx = (i < N) ? S.qp.s.f.ux[i] : 0.f;
+        usy = (i < N) ? S.qp.s.f.uy[i] : 0.f;
         tm.sync();
         return res;
     }

@@ -158,9 +158,34 @@ struct QPWork {
     int fail;
 };
 
+// Explicit-inverse workspace of the binary32 solver qp_solve_inv (see there).
+template <int NMAX>
+struct InvWork {
+    static constexpr int A = 2 * NMAX;                          // slots (active rows at most)
+    static constexpr int V = 2 * NMAX;                          // variables
+    // rows padded to A + 1 words: lanes walking their own rows hit distinct banks
+    float Mi[V][A + 1];      // M = N G^-1, variable x slot
+    float Bi[A][A + 1];      // B = G^-1, slot x slot
+    float r[A];
+    float lam[A], sax[A], say[A], sb[A];
+    int sia[A], sib[A], sk[A];
+    int act[A];              // active slots in order of addition
+    unsigned long long free_slots;
+};
+
+struct NoInvWork {};
+
+// binary32 work (the QP data and, for teams over 4 robots, the explicit-inverse factors)
+// overlays the binary64 re-solve work: the re-solve starts after the binary32 result is read.
+template <int NMAX>
+struct F32Work {
+    QPWork<float, NMAX> f;
+    typename std::conditional<(NMAX > 4), InvWork<NMAX>, NoInvWork>::type inv;
+};
+
 template <int NMAX>
 union QPUnion {
-    QPWork<float, NMAX> f;
+    F32Work<NMAX> s;
     QPWork<double, NMAX> d;
 };
 
@@ -178,7 +203,7 @@ template <typename Q, int NMAX>
 struct WorkSel;
 template <int NMAX>
 struct WorkSel<float, NMAX> {
-    static __device__ __forceinline__ QPWork<float, NMAX>& get(QPUnion<NMAX>& u) { return u.f; }
+    static __device__ __forceinline__ QPWork<float, NMAX>& get(QPUnion<NMAX>& u) { return u.s.f; }
 };
 template <int NMAX>
 struct WorkSel<double, NMAX> {
@@ -591,6 +616,359 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
 }
 
 // ------------------------------------------------------------------------------------------
+// The same dual active-set method in explicit-inverse form (binary32 teams of 8..32 lanes).
+// With N the active rows (as columns) and G = N^T N, it keeps B = G^-1 and M = N B in shared
+// memory, indexed by slot.  Then r = G^-1 N^T a_p = M^T a_p needs only the (at most four)
+// non-zeros of a_p -- one lane per active row, no sequential triangular solve -- and the block-
+// inverse identities update both in O(n q):
+//   add a_p (z = a_p - N r, s = |z|^2):  M <- [M - z r^T / s, z / s],
+//                                        B <- [[B + r r^T / s, -r / s], [-r^T / s, 1 / s]];
+//   drop row j:  M <- M_{:,-j} - M_{:,j} B_{j,-j} / B_jj,  B <- B_{-j,-j} - B_{-j,j} B_{j,-j} / B_jj.
+// ------------------------------------------------------------------------------------------
+
+// The barrier rows one lane evaluates in qp_solve_inv (teams with one robot per lane): its
+// circulant pair rows (partner, p_a - p_b, bound, key) and its four arena rows, computed once per
+// QP; "on" marks the ones currently in the active set.  key = row index * 32 + lane, so that an
+// argmax over keys breaks ties by row index and names the lane holding the row.
+template <int NMAX>
+struct LaneRows {
+    static constexpr int PR = NMAX / 2 > 0 ? NMAX / 2 : 1;
+    float dx[PR], dy[PR], bp[PR];
+    int j[PR], key[PR];
+    float bb[4];
+    int bkey[4];
+    int np;
+    unsigned on;  // bit d: pair row d active; bit PR + s: arena row s active
+};
+
+template <int NMAX>
+__device__ __forceinline__ void lane_rows_init(LaneRows<NMAX>& R, int i, int N, const float* px,
+                                               const float* py, const QPConsts<float>& c) {
+    const int nd = (N - 1) / 2;
+    R.np = (i < N) ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
+    R.on = 0u;
+    const int P = N * (N - 1) / 2;
+#pragma unroll
+    for (int d = 0; d < LaneRows<NMAX>::PR; ++d) {
+        int j = i + d + 1;
+        while (j >= N) j -= N;
+        if (d >= R.np) j = i;
+        const int a = min(i, j), b = max(i, j);
+        const float sg = (a == i) ? 1.f : -1.f;
+        R.j[d] = j;
+        R.key[d] = (d < R.np) ? pair_index(a, b, N) * 32 + (i & 31) : 0x7fffffff;
+        R.dx[d] = sg * (px[i < N ? i : 0] - px[j < N ? j : 0]);
+        R.dy[d] = sg * (py[i < N ? i : 0] - py[j < N ? j : 0]);
+        const float h = R.dx[d] * R.dx[d] + R.dy[d] * R.dy[d] - c.r2;
+        R.bp[d] = c.gamma * h * h * h;
+    }
+    const float pxi = px[i < N ? i : 0], pyi = py[i < N ? i : 0];
+    const float bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
+    const float by0 = c.ymax - c.half_r - pyi, by1 = pyi - c.ymin - c.half_r;
+    R.bb[0] = c.kg * bx0 * bx0 * bx0;
+    R.bb[1] = c.kg * bx1 * bx1 * bx1;
+    R.bb[2] = c.kg * by0 * by0 * by0;
+    R.bb[3] = c.kg * by1 * by1 * by1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) R.bkey[s] = (i < N) ? (P + 4 * i + s) * 32 + (i & 31) : 0x7fffffff;
+}
+
+// Most violated inactive row of the team at u (shared memory), its descriptor broadcast from
+// the lane that holds it.  Returns false when every row holds.
+template <int G, int NMAX>
+__device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NMAX>& R, int i,
+                                            const float* ux, const float* uy,
+                                            const QPConsts<float>& c, RowInfo<float>& p,
+                                            float& vbest) {
+    float vb = 0.f;
+    int kb = 0x7fffffff, ba = -1, bbv = -1;
+    float bdx = 0.f, bdy = 0.f, bbound = 0.f;
+    if (R.np > 0 || (R.bkey[0] != 0x7fffffff)) {
+        const float uxi = ux[i], uyi = uy[i];
+#pragma unroll
+        for (int d = 0; d < LaneRows<NMAX>::PR; ++d) {
+            if (d < R.np && !((R.on >> d) & 1u)) {
+                const int j = R.j[d];
+                const float sg = (i < j) ? 1.f : -1.f;
+                const float dux = sg * (uxi - ux[j]), duy = sg * (uyi - uy[j]);
+                const float v = -2.f * (R.dx[d] * dux + R.dy[d] * duy) - R.bp[d];
+                if (v > c.tol_abs + c.tol_rel * fabsf(R.bp[d]) &&
+                    (v > vb || (v == vb && R.key[d] < kb))) {
+                    vb = v;
+                    kb = R.key[d];
+                    ba = min(i, j);
+                    bbv = max(i, j);
+                    bdx = R.dx[d];
+                    bdy = R.dy[d];
+                    bbound = R.bp[d];
+                }
+            }
+        }
+        const float aus[4] = {uxi, -uxi, uyi, -uyi};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float v = aus[s] - R.bb[s];
+            if (R.bkey[s] != 0x7fffffff && !((R.on >> (LaneRows<NMAX>::PR + s)) & 1u) &&
+                v > c.tol_abs + c.tol_rel * fabsf(R.bb[s]) &&
+                (v > vb || (v == vb && R.bkey[s] < kb))) {
+                vb = v;
+                kb = R.bkey[s];
+                ba = i;
+                bbv = -1 - s;  // arena row s
+                bbound = R.bb[s];
+            }
+        }
+    }
+    tm.argmax(vb, kb);
+    vbest = vb;
+    if (kb == 0x7fffffff) return false;
+    const int own = kb & 31 & (G - 1);
+    const int a = __shfl_sync(tm.mask, ba, own, G), b = __shfl_sync(tm.mask, bbv, own, G);
+    const float dx = __shfl_sync(tm.mask, bdx, own, G), dy = __shfl_sync(tm.mask, bdy, own, G);
+    p.b = __shfl_sync(tm.mask, bbound, own, G);
+    p.k = kb;
+    p.ia = a;
+    if (b >= 0) {
+        p.ib = b;
+        p.ax = -2.f * dx;
+        p.ay = -2.f * dy;
+    } else {
+        const int s = -1 - b;
+        p.ib = -1;
+        p.ax = (s == 0) ? 1.f : (s == 1) ? -1.f : 0.f;
+        p.ay = (s == 2) ? 1.f : (s == 3) ? -1.f : 0.f;
+    }
+    return true;
+}
+
+// Mark row key k active / inactive in the lane that holds it.
+template <int NMAX>
+__device__ __forceinline__ void lane_rows_mark(LaneRows<NMAX>& R, int k, bool on) {
+#pragma unroll
+    for (int d = 0; d < LaneRows<NMAX>::PR; ++d)
+        if (R.key[d] == k) R.on = on ? (R.on | (1u << d)) : (R.on & ~(1u << d));
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (R.bkey[s] == k) {
+            const unsigned bit = 1u << (LaneRows<NMAX>::PR + s);
+            R.on = on ? (R.on | bit) : (R.on & ~bit);
+        }
+}
+
+template <int G, int NMAX>
+__device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, const QPConsts<float>& c,
+                                 QPWork<float, NMAX>& Wscan) {
+    constexpr int RPL = (NMAX + G - 1) / G;
+    constexpr int AS = InvWork<NMAX>::A;
+    if (tm.lane == 0) W.free_slots = (AS >= 64) ? ~0ull : ((1ull << AS) - 1ull);
+    tm.sync();
+    QPResult res;
+    res.status = 0;
+    res.q = 0;
+    res.iters = 0;
+    res.flag = false;
+    int q = 0;
+    static_assert(G >= NMAX, "qp_solve_inv holds one robot per lane");
+    LaneRows<NMAX> LR;
+    lane_rows_init<NMAX>(LR, tm.lane, N, Wscan.px, Wscan.py, c);
+    for (;;) {
+        float vbest;
+        RowInfo<float> p;
+        if (!scan_cached<G, NMAX>(tm, LR, tm.lane, Wscan.ux, Wscan.uy, c, p, vbest)) break;
+        if (++res.iters > c.max_iter || q >= AS) { res.status = 2; break; }
+        const float app = (p.ib >= 0 ? 2.f : 1.f) * (p.ax * p.ax + p.ay * p.ay);
+        // non-zeros of a_p: (variable, value)
+        const int v0 = 2 * p.ia, v1 = 2 * p.ia + 1;
+        const int v2 = p.ib >= 0 ? 2 * p.ib : v0, v3 = p.ib >= 0 ? 2 * p.ib + 1 : v1;
+        const float a0 = p.ax, a1 = p.ay, a2 = p.ib >= 0 ? -p.ax : 0.f, a3 = p.ib >= 0 ? -p.ay : 0.f;
+        float lam_p = 0.f;
+        bool added = false;
+        for (int guard = 0; guard <= AS + 1 && !added; ++guard) {
+            // r = M^T a_p over the active slots, one slot per lane
+            for (int idx = tm.lane; idx < q; idx += G) {
+                const int t = W.act[idx];
+                W.r[t] = W.Mi[v0][t] * a0 + W.Mi[v1][t] * a1 + W.Mi[v2][t] * a2 + W.Mi[v3][t] * a3;
+            }
+            tm.sync();
+            // z = a_p - N r on the lane's own robots
+            float zx[RPL], zy[RPL];
+            float zzl = 0.f;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+                const int i = tm.lane + s * G;
+                float ax = 0.f, ay = 0.f;
+                if (i < N) {
+                    if (p.ia == i) { ax += p.ax; ay += p.ay; }
+                    if (p.ib == i) { ax -= p.ax; ay -= p.ay; }
+                    for (int idx = 0; idx < q; ++idx) {
+                        const int t = W.act[idx];
+                        const float rt = W.r[t];
+                        if (W.sia[t] == i) { ax -= rt * W.sax[t]; ay -= rt * W.say[t]; }
+                        if (W.sib[t] == i) { ax += rt * W.sax[t]; ay += rt * W.say[t]; }
+                    }
+                }
+                zx[s] = ax;
+                zy[s] = ay;
+                zzl += ax * ax + ay * ay;
+            }
+            const float zz = tm.sum(zzl);
+            float td = CUDART_INF_F;
+            int jb = 0x7fffffff;
+            for (int idx = tm.lane; idx < q; idx += G) {
+                const int t = W.act[idx];
+                const float rt = W.r[t];
+                if (rt > 0.f) {
+                    const float tj = W.lam[t] / rt;
+                    if (tj < td || (tj == td && idx < jb)) { td = tj; jb = idx; }
+                }
+            }
+            tm.argmin(td, jb);
+            float apu;
+            if (p.ib >= 0)
+                apu = p.ax * (Wscan.ux[p.ia] - Wscan.ux[p.ib]) + p.ay * (Wscan.uy[p.ia] - Wscan.uy[p.ib]);
+            else
+                apu = p.ax * Wscan.ux[p.ia] + p.ay * Wscan.uy[p.ia];
+            const float sp = apu - p.b;
+            const bool indep = zz > c.eps_dep * app;
+            if (!indep) res.flag = true;
+            const float tf = indep ? sp / zz : CUDART_INF_F;
+            if (!(tf < CUDART_INF_F) && !(td < CUDART_INF_F)) { res.status = 1; break; }
+            const float st = tf < td ? tf : td;
+            tm.sync();  // every lane is done reading u, r, lam
+            if (tf < CUDART_INF_F) {
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        Wscan.ux[i] -= st * zx[s];
+                        Wscan.uy[i] -= st * zy[s];
+                    }
+                }
+            }
+            for (int idx = tm.lane; idx < q; idx += G) {
+                const int t = W.act[idx];
+                W.lam[t] -= st * W.r[t];
+            }
+            lam_p += st;
+            if (tf <= td) {
+                // add a_p in a free slot
+                const int sn = __ffsll((long long)W.free_slots) - 1;
+                const float inv = 1.f / zz;
+                // M <- [M - z r^T / zz, z / zz] on the lane's variables
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        for (int ax = 0; ax < 2; ++ax) {
+                            const int v = 2 * i + ax;
+                            const float zv = ax == 0 ? zx[s] : zy[s];
+                            for (int idx = 0; idx < q; ++idx) {
+                                const int t = W.act[idx];
+                                W.Mi[v][t] -= zv * W.r[t] * inv;
+                            }
+                            W.Mi[v][sn] = zv * inv;
+                        }
+                    }
+                }
+                // B <- [[B + r r^T / zz, -r / zz], [-r^T / zz, 1 / zz]]
+                for (int idx = tm.lane; idx < q; idx += G) {
+                    const int t = W.act[idx];
+                    const float rt = W.r[t] * inv;
+                    for (int jdx = 0; jdx < q; ++jdx) {
+                        const int u = W.act[jdx];
+                        W.Bi[t][u] += rt * W.r[u];
+                    }
+                    W.Bi[t][sn] = -rt;
+                    W.Bi[sn][t] = -rt;
+                }
+                tm.sync();
+                if (tm.lane == 0) {
+                    W.Bi[sn][sn] = inv;
+                    W.sia[sn] = p.ia;
+                    W.sib[sn] = p.ib;
+                    W.sax[sn] = p.ax;
+                    W.say[sn] = p.ay;
+                    W.sb[sn] = p.b;
+                    W.sk[sn] = p.k;
+                    W.lam[sn] = lam_p;
+                    W.act[q] = sn;
+                    W.free_slots &= ~(1ull << sn);
+                }
+                lane_rows_mark<NMAX>(LR, p.k, true);
+                ++q;
+                added = true;
+            } else {
+                // drop the blocking row (list position jb, slot j)
+                const int j = W.act[jb];
+                tm.sync();
+                const float bjj = W.Bi[j][j];
+                const float ibjj = 1.f / bjj;
+                // M <- M_{:,-j} - M_{:,j} B_{j,-j} / B_jj
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        for (int ax = 0; ax < 2; ++ax) {
+                            const int v = 2 * i + ax;
+                            const float mj = W.Mi[v][j] * ibjj;
+                            for (int idx = 0; idx < q; ++idx) {
+                                const int t = W.act[idx];
+                                if (t != j) W.Mi[v][t] -= mj * W.Bi[j][t];
+                            }
+                        }
+                    }
+                }
+                // B <- B_{-j,-j} - B_{-j,j} B_{j,-j} / B_jj (rows t != j; row j read only)
+                for (int idx = tm.lane; idx < q; idx += G) {
+                    const int t = W.act[idx];
+                    if (t == j) continue;
+                    const float btj = W.Bi[t][j] * ibjj;
+                    for (int jdx = 0; jdx < q; ++jdx) {
+                        const int u = W.act[jdx];
+                        if (u != j) W.Bi[t][u] -= btj * W.Bi[j][u];
+                    }
+                }
+                lane_rows_mark<NMAX>(LR, W.sk[j], false);
+                tm.sync();
+                if (tm.lane == 0) {
+                    for (int idx = jb; idx < q - 1; ++idx) W.act[idx] = W.act[idx + 1];
+                    W.free_slots |= 1ull << j;
+                }
+                --q;
+                if (!(bjj > 0.f)) res.status = 2;
+            }
+            tm.sync();
+            if (res.status != 0) break;
+        }
+        if (res.status != 0) break;
+        if (!added) { res.status = 2; break; }
+    }
+    res.q = q;
+    if (res.status == 0 && q > 0) {
+        bool small_h = false;
+        for (int idx = tm.lane; idx < q; idx += G) {
+            const int t = W.act[idx];
+            if (W.sib[t] >= 0) {
+                const float dx = Wscan.px[W.sia[t]] - Wscan.px[W.sib[t]];
+                const float dy = Wscan.py[W.sia[t]] - Wscan.py[W.sib[t]];
+                if (dx * dx + dy * dy - c.r2 < c.h_flag) small_h = true;
+            }
+        }
+        if (tm.any(small_h)) res.flag = true;
+    }
+    if (res.status == 1) {
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+            const int i = tm.lane + s * G;
+            if (i < N) { Wscan.ux[i] = 0.f; Wscan.uy[i] = 0.f; }
+        }
+    }
+    if (res.status != 0) res.flag = true;
+    tm.sync();
+    return res;
+}
+
+// ------------------------------------------------------------------------------------------
 // Small helpers
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ void sc_(float v, float* s, float* c) { sincosf(v, s, c); }
@@ -841,8 +1219,12 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
         }
         tm.sync();
 
-        // ---- barrier-certificate QP
-        QPResult res = qp_solve<R, G, NMAX>(tm, W, N, qc);
+        // ---- barrier-certificate QP (binary32: explicit-inverse form; binary64: Cholesky form)
+        QPResult res;
+        if constexpr (std::is_same<R, float>::value && (NMAX > 4))
+            res = qp_solve_inv<G, NMAX>(tm, S.qp.s.inv, N, qc, W);
+        else
+            res = qp_solve<R, G, NMAX>(tm, W, N, qc);
         int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
         R usx[RPL], usy[RPL];
         bool resolved = false;
@@ -1153,7 +1535,7 @@ __device__ void reset_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R,
 }
 
 template <typename R, int G, int NMAX>
-__global__ void __launch_bounds__(256) env_kernel(LaunchArgs<R> A) {
+__global__ void __launch_bounds__(256, 1) env_kernel(LaunchArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Team<G> tm;
     const int teams_per_block = blockDim.x / G;

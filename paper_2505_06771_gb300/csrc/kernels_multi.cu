@@ -1,7 +1,7 @@
 // kernels_multi.cu -- one persistent launch over environments of uneven robot counts (binary32).
 //
-// The envs of a batch are bucketed by robot count into classes (<= 4, <= 8, <= 16, <= 32
-// robots), each with its own team size (4, 8, 16, 32 lanes).  A block of 64 threads repeatedly
+// The envs of a batch are bucketed by robot count into classes (<= 4, <= 8, <= 16, <= 20,
+// <= 32 robots), each with its own team size (4, 8, 16, 32, 32 lanes).  A block of 64 threads repeatedly
 // takes the next work item -- a run of envs of one class, one env per team -- from a device-wide
 // queue (one atomic counter), and runs those envs for all T steps.  Items are ordered largest
 // class first, so the longest jobs start first and the short ones fill the tail.
@@ -48,6 +48,13 @@ __global__ void __launch_bounds__(64) env_kernel_multi(MultiArgs M) {
                 if (tib < w.z) run_env<float, 16, 16>(M.a, tm, *S, list[tib]);
                 break;
             }
+            case 20: {
+                const Team<32> tm;
+                const int tib = threadIdx.x / 32;
+                TeamSmem<float, 20>* S = reinterpret_cast<TeamSmem<float, 20>*>(smem_raw) + tib;
+                if (tib < w.z) run_env<float, 32, 20>(M.a, tm, *S, list[tib]);
+                break;
+            }
             default: {
                 const Team<32> tm;
                 const int tib = threadIdx.x / 32;
@@ -65,7 +72,8 @@ size_t multi_smem_bytes(unsigned class_mask) {
     if (class_mask & 1u) m = std::max(m, (size_t)(64 / 4) * sizeof(TeamSmem<float, 4>));
     if (class_mask & 2u) m = std::max(m, (size_t)(64 / 8) * sizeof(TeamSmem<float, 8>));
     if (class_mask & 4u) m = std::max(m, (size_t)(64 / 16) * sizeof(TeamSmem<float, 16>));
-    if (class_mask & 8u) m = std::max(m, (size_t)(64 / 32) * sizeof(TeamSmem<float, 32>));
+    if (class_mask & 8u) m = std::max(m, (size_t)(64 / 32) * sizeof(TeamSmem<float, 20>));
+    if (class_mask & 16u) m = std::max(m, (size_t)(64 / 32) * sizeof(TeamSmem<float, 32>));
     return m;
 }
 

@@ -9,8 +9,11 @@
 
 namespace rl {
 
-// Robot-count classes: an env with n robots runs in the smallest class with n <= nmax.
-constexpr int kClassNmax[4] = {4, 8, 16, 32};
+// Robot-count classes: an env with n robots runs in the smallest class with n <= nmax; the
+// team of a class has kClassLanes lanes (a power of two >= nmax).
+constexpr int kNumClasses = 5;
+constexpr int kClassNmax[kNumClasses] = {4, 8, 16, 20, 32};
+constexpr int kClassLanes[kNumClasses] = {4, 8, 16, 32, 32};
 
 // Launch the step (reset == false) or reset (reset == true) kernel of one class.
 // lanes: team size; block_threads: a multiple of 32; max_blocks <= 0: one team per env.
@@ -27,7 +30,7 @@ struct MultiClass {
 };
 struct MultiArgs {
     LaunchArgs<float> a;  // a.env_list: the class lists, concatenated
-    MultiClass cls[4];
+    MultiClass cls[kNumClasses];
     const int4* items;    // (class, first index in the class list, envs)
     int n_items;
     unsigned* head;       // work-queue counter, zeroed by launch_multi

@@ -52,7 +52,7 @@ struct rl_env {
     size_t seg_len[kSegs] = {};
     int32_t* d_lists = nullptr;
     std::vector<int32_t> h_nrob, h_off;
-    Class cls[4];
+    Class cls[rl::kNumClasses];
     int ncls = 0;
     std::string err;
     // rollout graph cache
@@ -373,7 +373,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     }
     // classes by robot count
     std::vector<int32_t> lists;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < rl::kNumClasses; ++c) {
         const int nm = rl::kClassNmax[c];
         const int lo = c == 0 ? 1 : rl::kClassNmax[c - 1] + 1;
         Class k;
@@ -384,10 +384,10 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         k.count = (int)lists.size() - k.begin;
         if (k.count == 0) continue;
         const unsigned ok = rl::supported_lanes(h->prec, nm);
-        int lanes = cfg->lanes > 0 ? cfg->lanes : nm;
-        if (!(lanes > 0 && (ok & (unsigned)lanes))) lanes = nm;
+        int lanes = cfg->lanes > 0 ? cfg->lanes : rl::kClassLanes[c];
+        if (!(lanes > 0 && (ok & (unsigned)lanes))) lanes = rl::kClassLanes[c];
         k.lanes = lanes;
-        k.block_threads = nm <= 8 ? 64 : (nm == 16 ? 64 : 32);
+        k.block_threads = nm <= 16 ? 64 : 32;
         k.warp_envs = cfg->warp_envs > 0 ? std::min(32, cfg->warp_envs) : 0;
         if (cfg->block_threads > 0) {
             if (cfg->block_threads % 32 != 0 || cfg->block_threads > 256) { rl_destroy(h); return RL_ERR_ARG; }
@@ -401,10 +401,12 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     std::vector<int4> items;
     if (h->prec == 32 && h->ncls > 1) {
         for (int c = h->ncls - 1; c >= 0; --c) {
-            const int tpb = 64 / h->cls[c].nmax;
+            int ci = 0;
+            while (rl::kClassNmax[ci] != h->cls[c].nmax) ++ci;
+            const int tpb = 64 / rl::kClassLanes[ci];
             for (int b = 0; b < h->cls[c].count; b += tpb)
                 items.push_back(make_int4(c, b, std::min(tpb, h->cls[c].count - b), 0));
-            h->class_mask |= 1u << (h->cls[c].nmax == 4 ? 0 : h->cls[c].nmax == 8 ? 1 : h->cls[c].nmax == 16 ? 2 : 3);
+            h->class_mask |= 1u << ci;
         }
         ce = cudaMallocAsync((void**)&h->d_items, items.size() * sizeof(int4) + 256, h->st);
         if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
@@ -558,7 +560,7 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     h->use_multi = 0;
     for (int c = 0; c < h->ncls && st == RL_OK; ++c) {
         const int nc = h->ncls;
-        Class all[4];
+        Class all[rl::kNumClasses];
         for (int i = 0; i < nc; ++i) all[i] = h->cls[i];
         h->cls[0] = all[c];
         h->ncls = 1;
@@ -615,7 +617,7 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     if (er != cudaSuccess) return cuda_fail(h, er, "rl_tune restore");
     if (h_choice) {
         h_choice[0] = h->use_multi;
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < rl::kNumClasses; ++c) {
             h_choice[1 + 4 * c] = c < h->ncls ? h->cls[c].nmax : 0;
             h_choice[2 + 4 * c] = c < h->ncls ? h->cls[c].lanes : 0;
             h_choice[3 + 4 * c] = c < h->ncls ? h->cls[c].block_threads : 0;

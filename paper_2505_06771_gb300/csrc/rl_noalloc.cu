@@ -121,10 +121,9 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     a.seed = seed;
 
     // the robot-count class this batch runs in, with its default lanes and block size
-    int nmax_class = 32;
-    for (int ci = 0; ci < 4; ++ci)
-        if (N <= rl::kClassNmax[ci]) { nmax_class = rl::kClassNmax[ci]; break; }
-    const int lanes = nmax_class;
+    int nmax_class = 32, lanes = 32;
+    for (int ci = 0; ci < rl::kNumClasses; ++ci)
+        if (N <= rl::kClassNmax[ci]) { nmax_class = rl::kClassNmax[ci]; lanes = rl::kClassLanes[ci]; break; }
     const int bt = nmax_class <= 16 ? 64 : 32;
     auto launch = [&](bool reset) -> cudaError_t {
         if constexpr (std::is_same<R, double>::value) {
