@@ -47,6 +47,14 @@ WORKLOADS = {
     "largen": dict(desc="navigation: 1024 envs x 20 robots x 300 steps, 30% near pairs, fp32 + "
                         "fp64 re-solve of flagged QPs",
                    scenario=0, E=1024, N=20, T=300, precision=32, near=0.3, n_max=20),
+    "waypoint": dict(desc="random waypoint navigation: 1 env x 4 robots x 10000 steps, a new goal "
+                          "on arrival within 0.05 m, fp32 (the single-env latency workload of "
+                          "the paper's Sec. 4.2, Table 2)",
+                     scenario=0, E=1, N=4, T=10000, precision=32, near=0.0, n_max=4,
+                     goal_eps=0.05, episode_len=10000,
+                     context={"paper_table2_ms_per_10k_steps": 9.18,
+                              "paper_hardware": "JAX on an Apple M4 Pro CPU (position "
+                                                "controller); another machine: context only"}),
 }
 
 
@@ -166,9 +174,14 @@ def _robots(w):
     return np.full(w["E"], w["N"], np.int32)
 
 
+def _cfg_overrides(w):
+    return dict(n_max=w["n_max"], near_frac=w["near"], goal_eps=w.get("goal_eps", 0.0),
+                episode_len=w.get("episode_len", 100))
+
+
 def _oracle_cfg(w):
     import oracle
-    return oracle.default_cfg(w["scenario"], n_max=w["n_max"], near_frac=w["near"])
+    return oracle.default_cfg(w["scenario"], **_cfg_overrides(w))
 
 
 def _cpu_baseline(w, budget_s: float = 20.0):
@@ -247,8 +260,7 @@ def _teacher_forced_error(rl, w, steps=8, envs=64):
 
     import oracle
     n = _robots(w)[:envs]
-    g = rl.config_default(w["scenario"], precision=w["precision"], n_max=w["n_max"],
-                          near_frac=w["near"])
+    g = rl.config_default(w["scenario"], precision=w["precision"], **_cfg_overrides(w))
     c = _oracle_cfg(w)
     env = rl.Env(g, len(n), n, 0)
     R = env.total_robots
@@ -301,8 +313,7 @@ def run_rollout(a):
     E, T = w["E"], w["T"]
     n = _robots(w)
     stream = torch.cuda.Stream()
-    g = rl.config_default(w["scenario"], precision=w["precision"], n_max=w["n_max"],
-                          near_frac=w["near"])
+    g = rl.config_default(w["scenario"], precision=w["precision"], **_cfg_overrides(w))
     fdt = torch.float64 if w["precision"] == 64 else torch.float32
     esz = 8 if w["precision"] == 64 else 4
     with torch.cuda.stream(stream):
@@ -315,7 +326,8 @@ def run_rollout(a):
     tuning = None
     if not a.no_tune and w["precision"] == 32:
         tuning = env.tune(min(50, T))
-    for _ in range(max(3, a.warmup)):
+    n_warm = max(3, a.warmup)
+    for _ in range(n_warm):
         env.rollout(T, obs, rew, done)
     stream.synchronize()
     if dist:
@@ -339,6 +351,8 @@ def run_rollout(a):
         torch.cuda.synchronize()
     total_ms = t_start.elapsed_time(t_end)
     per = [s.elapsed_time(e) for s, e in ev]
+    counters = env.counters()  # since the tuner: the warm-up and timed rollouts
+    env_steps_counted = E * T * (n_warm + a.steps)
     if dist:
         tt = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -396,8 +410,6 @@ def run_rollout(a):
                "d2h_bytes_per_step": int(h_obs.numel() * esz + h_rew.numel() * esz +
                                          h_done.numel())}
 
-    counters = env.counters()
-    env_steps_counted = max(1, int(counters[:, 6].sum()) * 100)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
                 "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": total_ms / a.steps,
@@ -405,7 +417,8 @@ def run_rollout(a):
                 "dtype": "f64" if w["precision"] == 64 else "f32", "data": "synthetic",
                 "config": {"workload": w["desc"], "n_envs": E,
                            "n_robots": w["N"] if w["N"] != "uneven" else "U{2..10}",
-                           "total_robots": rows, "horizon": T, "episode_len": 100,
+                           "total_robots": rows, "horizon": T,
+                           "episode_len": w.get("episode_len", 100),
                            "obs": f"[{T}, {rows}, {env.obs_dim}] per step",
                            "l2": f"trajectory outputs of {traj_bytes / 1e6:.0f} MB per step "
                                  "(larger than the 129 MB L2 except for the tiny workload)",
@@ -420,6 +433,11 @@ def run_rollout(a):
                 "qp": {"active_step_frac": float(counters[:, 3].sum()) / env_steps_counted,
                        "fp64_resolved_frac": float(counters[:, 4].sum()) / env_steps_counted,
                        "collisions": int(counters[:, 0].sum())}}
+        if w.get("goal_eps"):
+            line["waypoint_arrivals_per_10k_steps"] = \
+                1e4 * float(counters[:, 2].sum()) / env_steps_counted
+        if "context" in w:
+            line["context"] = w["context"]
         line.update(extra)
         if a.workload in ("largen", "uneven", "tiny"):
             line["parity_sample"] = _teacher_forced_error(rl, w)

@@ -61,7 +61,7 @@ typedef enum { RL_PREC_F32 = 32, RL_PREC_F64 = 64 } rl_precision;
 enum {
     RL_CNT_COLLISIONS = 0,   /* colliding pairs summed over steps: |p_i - p_j|^2 < r^2 */
     RL_CNT_OOB = 1,          /* robots whose projected point left the arena, summed over steps */
-    RL_CNT_SUCCESS = 2,      /* foraged resources */
+    RL_CNT_SUCCESS = 2,      /* foraged resources; Navigation with goal_eps > 0: arrivals */
     RL_CNT_QP_ACTIVE = 3,    /* steps whose QP had at least one active row */
     RL_CNT_QP_FLAGGED = 4,   /* steps whose binary32 QP was flagged and re-solved in binary64 */
     RL_CNT_QP_INFEASIBLE = 5,/* steps whose QP was infeasible (the env's robots then stop) */
@@ -103,6 +103,9 @@ typedef struct {
     double near_frac;       /* reset: share of envs with one near pair (0) */
     double near_dmin, near_dmax;     /* reset: distance of the near pair [m] (0.18, 0.20) */
     double h_flag;          /* flag a binary32 QP with an active pair whose h < h_flag (1e-3) */
+    double goal_eps;        /* Navigation: > 0 gives a robot a new goal when its projected point
+                               ends a step within goal_eps of its goal (Random Waypoint
+                               Navigation, Sec. 4.2); 0 (default) keeps goals for the episode */
 } rl_config;
 
 /* Optional outputs of one step (any pointer may be NULL). */
@@ -134,7 +137,10 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
 rl_status rl_reset(rl_env* env, uint64_t seed);
 
 /* One step of every env (Dec-POMDP step: joint action -> per-agent observations, team reward,
-   done).  d_actions is required unless the handle is scripted; the others may be NULL. */
+   done).  d_actions is required unless the handle is scripted; the others may be NULL.
+   A non-finite action (NaN or infinity) is taken as zero for that robot and raises a bit in
+   the handle's device status word, which the next rl_sync or rl_get_counters reports (once)
+   as RL_ERR_ARG. */
 rl_status rl_step(rl_env* env, const void* d_actions, void* d_obs, void* d_reward,
                   uint8_t* d_done);
 
@@ -173,10 +179,13 @@ size_t    rl_state_bytes(const rl_env* env);
 rl_status rl_get_state(rl_env* env, void* h_dst, size_t bytes);
 rl_status rl_set_state(rl_env* env, const void* h_src, size_t bytes);
 
-/* Counters [E][RL_NCOUNT] to host memory (synchronises the stream). */
+/* Counters [E][RL_NCOUNT] to host memory (synchronises the stream).  RL_ERR_ARG if the
+   device status word was raised (non-finite action, see rl_step); the counters are copied
+   all the same. */
 rl_status rl_get_counters(rl_env* env, int32_t* h_dst);
 
-/* Wait for the handle's stream; returns RL_ERR_CUDA if the device reported an error. */
+/* Wait for the handle's stream; RL_ERR_CUDA if the device reported a CUDA error, RL_ERR_ARG
+   if a non-finite action was seen since the last report (the word is then cleared). */
 rl_status rl_sync(rl_env* env);
 
 /* Allocation-free reset + rollout.  The paper has no counterpart: this is a service for callers

@@ -57,7 +57,7 @@ class Cfg(ctypes.Structure):
                [(n, ctypes.c_double) for n in
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
-                 "near_frac", "near_dmin", "near_dmax")]
+                 "near_frac", "near_dmin", "near_dmax", "goal_eps")]
 
 
 _P = ctypes.POINTER
@@ -114,7 +114,7 @@ def default_cfg(scenario: int = NAV, n_max: int = 4, **overrides) -> dict:
              gamma=100.0, r=0.17, l=0.05, vmax=0.2, wmax=3.6, dt=0.033, kappa=0.4, k_si=1.0,
              noise_amp=0.05, c_col=1.0 if scenario == NAV else 0.0, forage_radius=0.25,
              xmin=-1.6, xmax=1.6, ymin=-1.0, ymax=1.0, init_margin=0.2, min_sep=0.3,
-             near_frac=0.0, near_dmin=0.18, near_dmax=0.20)
+             near_frac=0.0, near_dmin=0.18, near_dmax=0.20, goal_eps=0.0)
     c.update(overrides)
     return c
 

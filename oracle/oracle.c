@@ -653,6 +653,28 @@ static void env_step(const orc_cfg* c, uint64_t seed, int e, env_t* s, const dou
             double d_new = hypot(px[i] - s->gx[i], py[i] - s->gy[i]);
             rew -= d_new - d_old[i];
         }
+        /* Random Waypoint Navigation (Sec. 4.2): a robot whose projected point ends the step
+           strictly within goal_eps of its goal is assigned a new goal (after the reward, which
+           uses the goal it was heading to), drawn from the reset's goal distribution under the
+           counter (env, episode, goal | robot, steps taken in the episode including this one).
+           Each arrival counts as a success. */
+        if (c->goal_eps > 0.0) {
+            const float lox = (float)c->xmin + (float)c->init_margin;
+            const float hix = (float)c->xmax - (float)c->init_margin;
+            const float loy = (float)c->ymin + (float)c->init_margin;
+            const float hiy = (float)c->ymax - (float)c->init_margin;
+            const float wx = hix - lox, wy = hiy - loy;
+            for (int i = 0; i < N; ++i) {
+                double dx = px[i] - s->gx[i], dy = py[i] - s->gy[i];
+                if (dx * dx + dy * dy < c->goal_eps * c->goal_eps) {
+                    uint32_t w[4];
+                    draw(seed, e, s->ep, P_GOAL, i, (uint32_t)(s->t + 1), w);
+                    s->gx[i] = (double)(lox + u01(w[0]) * wx);
+                    s->gy[i] = (double)(loy + u01(w[1]) * wy);
+                    cnt[ORC_CNT_SUCCESS] += 1;
+                }
+            }
+        }
     }
     rew -= c->c_col * (double)col;
 
@@ -682,6 +704,7 @@ static int check_cfg(const orc_cfg* c, int E, const int32_t* n_robots) {
     if (c->scenario == ORC_FORAGE && (c->n_res_min < 0 || c->n_res_max > c->r_max ||
                                       c->n_res_min > c->n_res_max))
         return 1;
+    if (!(c->goal_eps >= 0.0) || (c->goal_eps > 0.0 && c->scenario != ORC_NAV)) return 1;
     for (int e = 0; e < E; ++e)
         if (n_robots[e] < 1 || n_robots[e] > c->n_max) return 1;
     return 0;

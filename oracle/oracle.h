@@ -35,6 +35,8 @@ typedef struct {
     double gamma, r, l, vmax, wmax, dt, kappa, k_si, noise_amp, c_col, forage_radius;
     double xmin, xmax, ymin, ymax, init_margin, min_sep;
     double near_frac, near_dmin, near_dmax;
+    double goal_eps;       /* Navigation: > 0 assigns a new goal on arrival (Random Waypoint
+                              Navigation, Sec. 4.2); 0 keeps the goals for the episode */
 } orc_cfg;
 
 /* Batched structure-of-arrays state.  Robots of env e occupy [off_e, off_e + n_e). */

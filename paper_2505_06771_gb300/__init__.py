@@ -45,7 +45,7 @@ class RLConfig(ctypes.Structure):
                [(n, ctypes.c_double) for n in
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
-                 "near_frac", "near_dmin", "near_dmax", "h_flag")]
+                 "near_frac", "near_dmin", "near_dmax", "h_flag", "goal_eps")]
 
 
 class RLRequest(ctypes.Structure):

@@ -12,6 +12,7 @@
 // also goes through the shared-memory code of env_step.cuh.
 #pragma once
 #include "env_step.cuh"
+#include "qp_regs.cuh"
 
 namespace rl {
 
@@ -378,6 +379,40 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
     return res;
 }
 
+// The barrier QP of one env of N <= 4 robots, solved redundantly by every lane of the team.
+// One round of shuffles all-gathers the projected points and nominal velocities; then each lane
+// runs the register dual active-set solver (thread_qp: 22 row slots in tie-break order,
+// closed-form first iteration) on the whole 8-variable QP, with no cross-lane traffic inside
+// the solve, and keeps its own robot's u.  Every lane takes the same branches, so the team
+// never diverges; an active set beyond kRegRows rows goes to the shared-memory solver.
+__device__ __forceinline__ QPResult small_filter_all(const Team<4>& tm, TeamSmem<float, 4>& S,
+                                                     int N, float px, float py, float u0x,
+                                                     float u0y, const QPConsts<float>& c,
+                                                     float& usx, float& usy) {
+    float Px[4], Py[4], U0[8], U[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Px[j] = __shfl_sync(tm.mask, px, j, 4);
+        Py[j] = __shfl_sync(tm.mask, py, j, 4);
+        U0[2 * j] = __shfl_sync(tm.mask, u0x, j, 4);
+        U0[2 * j + 1] = __shfl_sync(tm.mask, u0y, j, 4);
+    }
+    bool overflow;
+    QPResult res = thread_qp<float, kRegRows>(Px, Py, N, U0, c, U, overflow);
+    if (overflow) {
+        res = small_general(tm, S, N, px, py, u0x, u0y, c);
+        const int i = tm.lane;
+        usx = (i < N) ? S.qp.s.f.ux[i] : 0.f;
+        usy = (i < N) ? S.qp.s.f.uy[i] : 0.f;
+        tm.sync();
+        return res;
+    }
+    const int i = tm.lane;
+    usx = (i == 0) ? U[0] : (i == 1) ? U[2] : (i == 2) ? U[4] : U[6];
+    usy = (i == 0) ? U[1] : (i == 1) ? U[3] : (i == 2) ? U[5] : U[7];
+    return res;
+}
+
 // binary64 re-solve of a flagged QP by the team, through the shared-memory solver.
 static __device__ __noinline__ QPResult small_resolve_f64(const Team<4> tm, TeamSmem<float, 4>& S,
                                                    const StepConsts<float> k, int N, float x,
@@ -551,6 +586,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         if (!FAST && acts) {
             ux = acts[2 * row];
             uy = acts[2 * row + 1];
+            screen_action(A.io.status, ux, uy);
         } else {
             float tx = gx, ty = gy;
             if (forage) small_forage_target(S, n_res, px, py, tx, ty);
@@ -587,7 +623,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         const float dold = fast_norm(px - gx, py - gy);
         // ---- the barrier QP
         float usx, usy;
-        QPResult res = small_filter(tm, S, N, jn, ndi, px, py, ux, uy, qc, usx, usy);
+        QPResult res = small_filter_all(tm, S, N, px, py, ux, uy, qc, usx, usy);
         int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
         if (k.resolve_f64 && res.flag) {
             const QPResult r64 = small_resolve_f64(tm, S, k, N, x, y, th, ux, uy);
@@ -626,12 +662,23 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
             flags_l += (d < ndi && dx * dx + dy * dy < k.r2) ? 1 : 0;
         }
         flags_l += (own && (npx < k.xmin || npx > k.xmax || npy < k.ymin || npy > k.ymax)) ? 65536 : 0;
+        // flags_l: collisions in bits 0..7, waypoint arrivals in 8..15, out-of-arena from 16
         float rew_l = (!forage && own) ? dold - fast_norm(npx - gx, npy - gy) : 0.f;
+        if (!forage && k.waypoint && own) {
+            const float ex = npx - gx, ey = npy - gy;
+            if (ex * ex + ey * ey < k.goal_eps2) {
+                const float2 g = waypoint_goal(A.seed, A.sc.lox, A.sc.loy, A.sc.wx, A.sc.wy, e,
+                                               ep, i, t + 1);
+                gx = g.x;
+                gy = g.y;
+                flags_l += 256;  // arrivals in bits 8..15
+            }
+        }
         const int flags = tm.sum(flags_l);
         float rew = tm.sum(rew_l);
-        const int col = flags & 0xffff, oob = flags >> 16;
+        const int col = flags & 0xff, oob = flags >> 16;
         bool all_foraged = false;
-        int succ = 0;
+        int succ = (flags >> 8) & 0xff;
         if (forage) {
             int remaining = 0;
             for (int r = 0; r < n_res; ++r) {

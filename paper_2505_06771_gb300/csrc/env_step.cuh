@@ -40,8 +40,9 @@ template <typename R>
 struct StepConsts {
     R gamma, r2, l, inv_l, vmax, half_track, inv_track, dt, kg, half_r, k_si, c_col, rho2;
     R xmin, xmax, ymin, ymax, h_flag;
+    R goal_eps2;        // Navigation waypoints: squared arrival radius (waypoint != 0)
     int scenario, scripted, episode_len, max_iter, n_res_min, n_res_max, r_max, n_max_obs;
-    int max_attempts, resolve_f64, noise_on;
+    int max_attempts, resolve_f64, noise_on, waypoint;
     float noise_scale;  // 2 * noise amplitude, binary32 (the noise draw is binary32)
 };
 
@@ -74,10 +75,25 @@ struct StepIO {
     R* vw;
     int32_t* qp_info;  // [E][4]
     R* ret;            // [E] sum of the rewards of this launch (serving), or NULL
+    int32_t* status;   // device status word (host-mapped), or NULL; see flag_status
     long long obs_step;  // rows * obs_dim
     int E;
     int obs_dim;
 };
+
+// Bits of the device status word.  Set by any lane, read and cleared by the host.
+constexpr int32_t kStatusNonFiniteAction = 1;
+
+// A non-finite policy action is replaced by zero (the robot's nominal velocity is zero, the
+// barrier QP still applies) and reported through the status word.
+template <typename R>
+__device__ __forceinline__ void screen_action(int32_t* status, R& ux, R& uy) {
+    if (!(isfinite(ux) && isfinite(uy))) {
+        ux = (R)0;
+        uy = (R)0;
+        if (status) *(volatile int32_t*)status = kStatusNonFiniteAction;
+    }
+}
 
 template <typename R>
 struct LaunchArgs {
@@ -1103,6 +1119,17 @@ __device__ void team_sample(const Team<G>& tm, TeamSmem<R, NMAX>& S, const Launc
     tm.sync();
 }
 
+// New goal of a robot that arrived at its goal (Random Waypoint Navigation, Sec. 4.2): the
+// reset's goal distribution under the counter (env, episode, goal | robot, steps taken in the
+// episode including this one), so it never repeats the reset's draw (counter word 3 = 0).
+// Out of line: arrivals are rare and the hot loop stays small.
+static __device__ __noinline__ float2 waypoint_goal(uint64_t seed, float lox, float loy, float wx,
+                                                    float wy, int e, int ep, int i, int t_after) {
+    const Words4 w = draw(seed, e, ep, kGoal, i, (uint32_t)t_after);
+    return make_float2(__fadd_rn(lox, __fmul_rn(unit24(w.w[0]), wx)),
+                       __fadd_rn(loy, __fmul_rn(unit24(w.w[1]), wy)));
+}
+
 // Goal and level of robot i for episode ep (owner lane).
 template <typename R>
 __device__ __forceinline__ void robot_goal_level(const LaunchArgs<R>& A, int e, int ep, int i,
@@ -1183,6 +1210,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 if (A.io.actions) {
                     ux = A.io.actions[2 * (off + i)];
                     uy = A.io.actions[2 * (off + i) + 1];
+                    screen_action(A.io.status, ux, uy);
                 } else {
                     R tx = gx[s], ty = gy[s];
                     if (forage) {
@@ -1310,7 +1338,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
         tm.sync();
 
         // ---- flags and reward
-        int col_l = 0, oob_l = 0;
+        int col_l = 0, oob_l = 0, arr_l = 0;
         R rew_l = (R)0;
         const int nd = (N - 1) / 2;
 #pragma unroll
@@ -1327,13 +1355,23 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 }
                 if (pxi < k.xmin || pxi > k.xmax || pyi < k.ymin || pyi > k.ymax) ++oob_l;
                 if (!forage) rew_l -= hyp(pxi - gx[s], pyi - gy[s]) - dold[s];
+                if (!forage && k.waypoint) {
+                    const R ex = pxi - gx[s], ey = pyi - gy[s];
+                    if (ex * ex + ey * ey < k.goal_eps2) {
+                        const float2 g = waypoint_goal(A.seed, A.sc.lox, A.sc.loy, A.sc.wx,
+                                                       A.sc.wy, e, ep, i, t + 1);
+                        gx[s] = (R)g.x;
+                        gy[s] = (R)g.y;
+                        ++arr_l;
+                    }
+                }
             }
         }
         const int col = tm.sum(col_l);
         const int oob = tm.sum(oob_l);
         R rew = tm.sum(rew_l);
         bool all_foraged = false;
-        int succ = 0;
+        int succ = k.waypoint ? tm.sum(arr_l) : 0;
         if (forage) {
             const R rho2 = k.rho2;
             int remaining = 0;

@@ -69,6 +69,8 @@ struct rl_env {
     int4* d_items = nullptr;
     unsigned* d_head = nullptr;
     unsigned class_mask = 0;
+    // device status word (rl::kStatusNonFiniteAction ...), read by the synchronising calls
+    int32_t* d_status = nullptr;
 };
 
 namespace {
@@ -94,6 +96,10 @@ bool valid_cfg(const rl_config& c, std::string& why) {
         if (c.n_res_min < 0 || c.n_res_max > c.r_max || c.n_res_min > c.n_res_max) { why = "n_res"; return false; }
     }
     if (c.n_max < 0 || c.n_max > rl::kMaxRobots) { why = "n_max"; return false; }
+    if (!(c.goal_eps >= 0.0) || (c.goal_eps > 0.0 && c.scenario != RL_SCEN_NAVIGATION)) {
+        why = "goal_eps";
+        return false;
+    }
     return true;
 }
 
@@ -111,6 +117,7 @@ void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
     a.s.off = (const int32_t*)seg(S_OFF);
     a.s.nrob = (const int32_t*)seg(S_NROB);
     std::memset(&a.io, 0, sizeof(a.io));
+    a.io.status = h->d_status;
     a.io.E = h->E;
     a.io.obs_dim = h->obs_dim;
     a.io.obs_step = (long long)h->total * h->obs_dim;
@@ -122,6 +129,8 @@ void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
     k.c_col = (R)c.c_col; k.rho2 = (R)(c.forage_radius * c.forage_radius);
     k.xmin = (R)c.xmin; k.xmax = (R)c.xmax; k.ymin = (R)c.ymin; k.ymax = (R)c.ymax;
     k.h_flag = (R)c.h_flag;
+    k.goal_eps2 = (R)(c.goal_eps * c.goal_eps);
+    k.waypoint = (c.scenario == RL_SCEN_NAVIGATION && c.goal_eps > 0.0) ? 1 : 0;
     k.scenario = c.scenario; k.scripted = c.scripted; k.episode_len = c.episode_len;
     k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * h->n_max + 16;
     k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = h->r_max;
@@ -264,6 +273,23 @@ rl_status rollout_enqueue(rl_env* h, int T, void* obs, void* rew, uint8_t* done)
                          : do_rollout_launch<float>(h, T, obs, rew, done);
 }
 
+// Wait for the stream, then report (once) what the kernels raised in the status word.
+rl_status sync_and_take_status(rl_env* h, const char* what) {
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->d_status, sizeof(v), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    if (v == 0) return RL_OK;
+    e = cudaMemsetAsync(h->d_status, 0, sizeof(v), h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    if (v & rl::kStatusNonFiniteAction)
+        return fail(h, RL_ERR_ARG, std::string(what) +
+                                       ": a non-finite action reached the device (that robot's "
+                                       "nominal velocity was taken as zero)");
+    return fail(h, RL_ERR_STATE, std::string(what) + ": device status word set");
+}
+
 void drop_graph(rl_env* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -397,6 +423,10 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     }
     cudaError_t ce = cudaMallocAsync((void**)&h->d_lists, lists.size() * sizeof(int32_t), h->st);
     if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
+    ce = cudaMallocAsync((void**)&h->d_status, 256, h->st);
+    if (ce != cudaSuccess) { cudaGetLastError(); rl_destroy(h); return RL_ERR_OOM; }
+    ce = cudaMemsetAsync(h->d_status, 0, 256, h->st);
+    if (ce != cudaSuccess) { rl_destroy(h); return RL_ERR_CUDA; }
     // work items of the one-launch path, largest class first
     std::vector<int4> items;
     if (h->prec == 32 && h->ncls > 1) {
@@ -715,17 +745,13 @@ rl_status rl_get_counters(rl_env* h, int32_t* dst) {
     if (!h || !dst) return RL_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(dst, h->d_img + h->seg_off[S_COUNTERS],
                                     h->seg_len[S_COUNTERS], cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_counters");
-    return RL_OK;
+    return sync_and_take_status(h, "get_counters");
 }
 
 rl_status rl_sync(rl_env* h) {
     if (!h) return RL_ERR_ARG;
-    cudaError_t e = cudaStreamSynchronize(h->st);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
-    return RL_OK;
+    return sync_and_take_status(h, "sync");
 }
 
 int32_t rl_obs_dim(const rl_env* h) { return h ? h->obs_dim : 0; }
@@ -743,6 +769,7 @@ void rl_destroy(rl_env* h) {
     if (h->d_lists) cudaFreeAsync(h->d_lists, h->st);
     if (h->d_items) cudaFreeAsync(h->d_items, h->st);
     if (h->d_img) cudaFreeAsync(h->d_img, h->st);
+    if (h->d_status) cudaFreeAsync(h->d_status, h->st);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
 }

@@ -95,6 +95,8 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     k.c_col = (R)c.c_col; k.rho2 = (R)(c.forage_radius * c.forage_radius);
     k.xmin = (R)c.xmin; k.xmax = (R)c.xmax; k.ymin = (R)c.ymin; k.ymax = (R)c.ymax;
     k.h_flag = (R)c.h_flag;
+    k.goal_eps2 = (R)(c.goal_eps * c.goal_eps);
+    k.waypoint = (c.scenario == RL_SCEN_NAVIGATION && c.goal_eps > 0.0) ? 1 : 0;
     k.scenario = c.scenario; k.scripted = 1; k.episode_len = c.episode_len;
     k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * n_max + 16;
     k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = r_max;
@@ -177,6 +179,8 @@ extern "C" rl_status rl_rollout_noalloc(const rl_config* cfg, int32_t n_envs, in
         return RL_ERR_ARG;
     if (!(c.l > 0) || !(c.vmax > 0) || !(c.wmax > 0) || !(c.dt > 0) || !(c.xmax > c.xmin) ||
         !(c.ymax > c.ymin))
+        return RL_ERR_ARG;
+    if (!(c.goal_eps >= 0.0) || (c.goal_eps > 0.0 && c.scenario != RL_SCEN_NAVIGATION))
         return RL_ERR_ARG;
     if (rl_noalloc_state_bytes(cfg, n_envs, n_robots) > kStaticBytes) return RL_ERR_ARG;
     void* base = nullptr;

@@ -116,6 +116,9 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
                                               g["n_max"], g["r_max"]))
         assert np.array_equal(st2["t"], s.t) and np.array_equal(st2["ep"], s.ep)
         assert np.array_equal(st2["level"], s.level)
+        # goals change only through exact draws (reset, waypoint arrival)
+        assert np.array_equal(st2["gx"].astype(np.float64), s.gx), f"goals differ at step {t}"
+        assert np.array_equal(st2["gy"].astype(np.float64), s.gy), f"goals differ at step {t}"
         if o["r_max"] > 0:
             assert np.array_equal(st2["qactive"], s.qactive), f"resources differ at step {t}"
         cg, co = st2["counters"], s.counters.reshape(-1, 8)
@@ -167,6 +170,45 @@ def test_teacher_forced_thread_kernel(rl, N, E):
     print(f"\nthread kernel N={N}: max errors {err}")
     assert err["pose"] < 1e-6 and err["th"] < 2e-5
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
+
+
+@pytest.mark.parametrize("case", ["nav4", "nav4_thread", "nav3", "nav10", "nav4_f64"])
+def test_teacher_forced_waypoints(rl, case):
+    """Random Waypoint Navigation (goal reassigned on arrival): every kernel that runs 4-robot,
+    3-robot, 10-robot and binary64 Navigation against the oracle stepped from the same state.
+    The arrival radius is large so that arrivals happen within the 40 steps; goals, arrival
+    counts and done flags are compared exactly."""
+    N = {"nav4": 4, "nav4_thread": 4, "nav3": 3, "nav10": 10, "nav4_f64": 4}[case]
+    prec = 64 if case == "nav4_f64" else 32
+    g, o = make_pair(0, N, prec, goal_eps=0.35, episode_len=10_000)
+    E = 96 if N == 10 else 300
+    err, _ = _teacher_forced(rl, g, o, [N] * E, 23, 40, traces=(case != "nav4_thread"))
+    print(f"\nwaypoints {case}: max errors {err}")
+    tol = 1e-5 if prec == 64 else 1.0
+    assert err["pose"] < 1e-6 * tol and err["rew"] < 1e-5 * tol and err["obs"] < 1e-5 * tol
+
+
+def test_waypoint_arrivals_counted_in_rollout(rl):
+    """Rollout (persistent kernel) and step-at-a-time agree in waypoint mode, and arrivals are
+    counted: the success counter equals the number of goal changes seen in the observations."""
+    g, _ = make_pair(0, 4, goal_eps=0.2, episode_len=10_000)
+    n, T = [4] * 64, 120
+    a = rl.Env(g, 64, n, 4)
+    bt = _alloc(a, T)
+    a.rollout(T, **bt)
+    b = rl.Env(g, 64, n, 4)
+    for t in range(T):
+        bs = _alloc(b)
+        b.step(obs=bs["obs"], reward=bs["reward"], done=bs["done"])
+        assert torch.equal(bs["obs"], bt["obs"][t]) and torch.equal(bs["done"], bt["done"][t])
+    assert a.get_state() == b.get_state()
+    goals = bt["obs"][:, :, 3:5].cpu().numpy()
+    changes = (np.abs(np.diff(goals, axis=0)).sum(-1) > 0).reshape(T - 1, 64, 4).sum()
+    first = a.state_arrays()  # counters include the arrivals of step 0 as well
+    succ = int(first["counters"][:, 2].sum())
+    assert succ >= changes > 0
+    a.close()
+    b.close()
 
 
 def test_teacher_forced_binary64(rl):
@@ -300,6 +342,39 @@ def test_argument_errors(rl):
         rl.Env(dict(g, episode_len=0), 8, 4, 0)
     with pytest.raises(rl.RLError):
         rl.Env(g, 8, 33, 0)
+
+
+@pytest.mark.parametrize("n_robots", [4, 10])
+def test_nonfinite_action_zeroed_and_reported(rl, n_robots):
+    """A NaN or infinite policy action is taken as zero for that robot (the step is the same as
+    with a zero action) and the next synchronising call reports it once as RL_ERR_ARG."""
+    g, _ = make_pair(0, n_robots, scripted=0)
+    E = 8
+    bad = rl.Env(g, E, n_robots, 5)
+    ref = rl.Env(g, E, n_robots, 5)
+    gen = torch.Generator().manual_seed(2)
+    act = ((torch.rand(E * n_robots, 2, generator=gen) - 0.5) * 0.3).cuda()
+    a_bad, a_ref = act.clone(), act.clone()
+    a_bad[3, 0] = float("nan")
+    a_bad[n_robots + 1, 1] = float("inf")
+    a_ref[3] = 0.0
+    a_ref[n_robots + 1] = 0.0
+    ob, orf = _alloc(bad), _alloc(ref)
+    bad.step(actions=a_bad, **ob)
+    ref.step(actions=a_ref, **orf)
+    with pytest.raises(rl.RLError) as ei:
+        bad.sync()
+    assert ei.value.status == 1 and "non-finite" in str(ei.value)
+    ref.sync()
+    bad.sync()  # reported once, then cleared
+    assert torch.equal(ob["obs"], orf["obs"]) and torch.equal(ob["reward"], orf["reward"])
+    assert torch.isfinite(ob["obs"]).all()
+    bad.step(actions=a_bad, **ob)
+    with pytest.raises(rl.RLError):
+        bad.counters()
+    bad.sync()
+    bad.close()
+    ref.close()
 
 
 @pytest.mark.parametrize("scenario", [0, 1])

@@ -199,3 +199,67 @@ def test_foraging_done_when_all_foraged():
     # radius covers the arena: every resource whose level <= summed robot levels goes at once
     assert done.sum() >= 1
     assert np.all(s.counters.reshape(16, 8)[:, oracle.CNT_SUCCESS] >= 2 * done)
+
+
+def _goal_draw(seed, e, ep, i, ctr):
+    """Goal of the reset's distribution under Philox counter word 3 = ctr (binary32 mapping)."""
+    f32 = np.float32
+    w = oracle.philox4x32_10([e, ep, (3 << 24) | i, ctr], [seed & 0xFFFFFFFF, seed >> 32])
+    u = [f32(np.uint32(v) >> np.uint32(8)) * f32(2.0 ** -24) for v in w[:2]]
+    lox, loy = f32(-1.6) + f32(0.2), f32(-1.0) + f32(0.2)
+    wx, wy = (f32(1.6) - f32(0.2)) - lox, (f32(1.0) - f32(0.2)) - loy
+    return float(lox + u[0] * wx), float(loy + u[1] * wy)
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.4])
+def test_waypoint_goal_reassigned_on_arrival(eps):
+    """Random Waypoint Navigation (Sec. 4.2): a robot whose new projected point lies strictly
+    within goal_eps of its goal gets a new goal from the goal stream at counter t + 1; the others
+    keep theirs; the reward of the step uses the old goals; each arrival is one success."""
+    N, E, seed = 4, 24, 17
+    c = oracle.default_cfg(n_max=N, episode_len=10_000, goal_eps=eps)
+    s = oracle.reset(c, seed, [N] * E)
+    # robot 0 of every env starts on its goal, so arrivals happen at once
+    px, py = _proj(s)
+    s.gx[0::N], s.gy[0::N] = px[0::N], py[0::N]
+    arrivals = 0
+    for _ in range(40):
+        before = s.copy()
+        _, rew, done, _ = oracle.step(c, seed, s)
+        assert not done.any()
+        p0x, p0y = _proj(before)
+        p1x, p1y = _proj(s)
+        for e in range(E):
+            d_rew = 0.0
+            for i in range(N):
+                g = N * e + i
+                d_rew -= (np.hypot(p1x[g] - before.gx[g], p1y[g] - before.gy[g])
+                          - np.hypot(p0x[g] - before.gx[g], p0y[g] - before.gy[g]))
+                d2 = (p1x[g] - before.gx[g]) ** 2 + (p1y[g] - before.gy[g]) ** 2
+                assert abs(d2 - eps * eps) > 1e-12  # no tie at this seed
+                if d2 < eps * eps:
+                    arrivals += 1
+                    exp = _goal_draw(seed, e, before.ep[e], i, before.t[e] + 1)
+                    assert (s.gx[g], s.gy[g]) == exp
+                else:
+                    assert (s.gx[g], s.gy[g]) == (before.gx[g], before.gy[g])
+            col = sum(1 for i, j in itertools.combinations(range(N), 2)
+                      if (p1x[N * e + i] - p1x[N * e + j]) ** 2
+                      + (p1y[N * e + i] - p1y[N * e + j]) ** 2 < 0.17 ** 2)
+            assert abs(rew[e] - (d_rew - col)) < 1e-12
+    assert arrivals >= E
+    assert int(s.counters.reshape(E, 8)[:, oracle.CNT_SUCCESS].sum()) == arrivals
+
+
+def test_waypoint_off_keeps_goals_and_rejects_foraging():
+    N, E = 4, 16
+    c = oracle.default_cfg(n_max=N, episode_len=10_000)
+    s = oracle.reset(c, 3, [N] * E)
+    g0 = (s.gx.copy(), s.gy.copy())
+    for _ in range(300):
+        oracle.step(c, 3, s)
+    assert np.array_equal(s.gx, g0[0]) and np.array_equal(s.gy, g0[1])
+    assert s.counters.reshape(E, 8)[:, oracle.CNT_SUCCESS].sum() == 0
+    cf = oracle.default_cfg(oracle.FORAGE, n_max=N, goal_eps=0.05)
+    with pytest.raises(Exception):
+        oracle.reset(cf, 3, [N] * E)
