@@ -325,7 +325,7 @@ def run_rollout(a):
     stream.synchronize()
     tuning = None
     if not a.no_tune and w["precision"] == 32:
-        tuning = env.tune(min(50, T))
+        tuning = env.tune(min(100, T))
     n_warm = max(3, a.warmup)
     for _ in range(n_warm):
         env.rollout(T, obs, rew, done)

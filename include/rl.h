@@ -86,6 +86,10 @@ typedef struct {
     int32_t lanes;          /* lanes per environment (0: the class default or rl_tune's pick) */
     int32_t block_threads;  /* threads per block, a multiple of 32 up to 256 (0: default) */
     int32_t warp_envs;      /* 4-robot binary32 class: envs per 32-lane warp (0: default) */
+    int32_t small_variant;  /* 4-robot binary32 Navigation, scripted, without traces: 1 the team
+                               kernel that reduces across lanes with shuffles (faster on large
+                               batches), 2 the team kernel that publishes each robot's state in
+                               shared memory (lower latency per step); 0 picks by batch size */
     double gamma;           /* barrier gain (100) */
     double r;               /* safety radius [m] (0.17) */
     double l;               /* projection distance [m] (0.05) */
@@ -162,8 +166,9 @@ rl_status rl_rollout_plain(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew
    state, restored afterwards) for every launch shape -- lanes per environment and threads per
    block for each robot-count class, and for an uneven batch one persistent launch over all
    classes against one launch per class -- and keeps the fastest for later rollouts.
-   h_choice (NULL or 21 ints): [one-launch flag, then per robot-count class (nmax, lanes,
-   block threads, envs per warp)].
+   h_choice (NULL or 26 ints): [one-launch flag, then per robot-count class (nmax, lanes,
+   block threads, envs per warp, 4-robot kernel variant)].
+   The probes write their trajectories to scratch memory the call allocates and frees.
    Synchronises the stream.  RL_ERR_STATE if the handle is not scripted. */
 rl_status rl_tune(rl_env* env, int32_t T_probe, int32_t* h_choice);
 

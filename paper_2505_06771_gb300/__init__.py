@@ -41,7 +41,7 @@ class RLConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("scenario", "precision", "scripted", "episode_len", "n_res_min", "n_res_max",
                  "r_max", "n_max", "max_attempts", "qp_max_iter", "resolve_f64", "lanes",
-                 "block_threads", "warp_envs")] + \
+                 "block_threads", "warp_envs", "small_variant")] + \
                [(n, ctypes.c_double) for n in
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
@@ -258,14 +258,14 @@ class Env:
 
     def tune(self, T_probe: int = 50) -> dict:
         """rl_tune: pick the fastest launch shape for this batch; returns the choice."""
-        out = np.zeros(21, np.int32)
+        out = np.zeros(26, np.int32)
         self._check(self._L.rl_tune(self._h, T_probe, out.ctypes.data), "rl_tune")
         self.lanes = int(self._L.rl_lanes(self._h))
         return {"one_launch": bool(out[0]),
-                "classes": [dict(nmax=int(out[1 + 4 * c]), lanes=int(out[2 + 4 * c]),
-                                 block_threads=int(out[3 + 4 * c]),
-                                 warp_envs=int(out[4 + 4 * c]))
-                            for c in range(5) if out[1 + 4 * c] > 0]}
+                "classes": [dict(nmax=int(out[1 + 5 * c]), lanes=int(out[2 + 5 * c]),
+                                 block_threads=int(out[3 + 5 * c]),
+                                 warp_envs=int(out[4 + 5 * c]), variant=int(out[5 + 5 * c]))
+                            for c in range(5) if out[1 + 5 * c] > 0]}
 
     def state_bytes(self) -> int:
         return int(self._L.rl_state_bytes(self._h))

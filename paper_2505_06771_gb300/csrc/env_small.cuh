@@ -812,24 +812,4 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     }
 }
 
-// A.warp_envs teams (envs) per 32-lane warp, 1..8 (0: 4); with fewer than 8 the other lanes
-// idle, which trades SIMD width for less divergence between envs and more warps per scheduler
-// (4 per warp measured fastest for 4096 envs of 4 robots).
-template <bool FAST>
-__global__ void __launch_bounds__(128, 1) env_kernel_small(LaunchArgs<float> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Team<4> tm;
-    const int per = (A.warp_envs >= 1 && A.warp_envs <= 8) ? A.warp_envs : 4;
-    const int tiw = (threadIdx.x & 31) >> 2;  // team in warp
-    if (tiw >= per) return;
-    const int tib = threadIdx.x / 4;
-    TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + tib;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int idx = warp * per + tiw; idx < A.n_list; idx += warps * per) {
-        const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
-        run_env_small<FAST>(A, tm, *S, e);
-    }
-}
-
 }  // namespace rl

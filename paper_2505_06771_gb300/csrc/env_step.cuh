@@ -106,6 +106,7 @@ struct LaunchArgs {
     int env_begin;
     int T;
     int warp_envs;  // one-thread-per-env kernel: envs per 32-lane warp
+    int variant;    // 4-robot binary32 Navigation fast path: 1 shuffle team, 2 gather team
     uint64_t seed;
 };
 
@@ -207,6 +208,8 @@ union QPUnion {
 
 template <typename R, int NMAX>
 struct TeamSmem {
+    float4 g4[4][2];     // 4-robot Navigation kernel: per-robot state published each step
+    float2 g2[4];        // and nominal velocities
     QPUnion<NMAX> qp;
     R sx[NMAX], sy[NMAX], sth[NMAX];
     int slevel[NMAX];

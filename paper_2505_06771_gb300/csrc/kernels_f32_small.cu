@@ -1,7 +1,7 @@
 // Binary32 kernels of the 4-robot class: one thread per env (Navigation, scripted, no traces),
 // the register-resident team kernel (4 lanes per env), and the generic shared-memory kernel with
 // 2 lanes per env (a tuner candidate).
-#include "env_small.cuh"
+#include "env_nav4.cuh"
 #include "env_thread.cuh"
 #include "launch.h"
 
@@ -17,7 +17,19 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     const size_t smem = (size_t)tpb * sizeof(TeamSmem<float, 4>);
     const bool fast = is_fast(a);
     const int per = (a.warp_envs >= 1 && a.warp_envs <= 8) ? a.warp_envs : 4;
-    void (*kern)(LaunchArgs<float>) = fast ? env_kernel_small<true> : env_kernel_small<false>;
+    int variant = a.variant;
+    if (fast && variant != 1 && variant != 2) {
+        // auto: the gather kernel while the batch leaves schedulers idle (its latency per step
+        // is lower), the shuffle kernel once there are more warps than schedulers
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const long long warps = ((long long)a.n_list + per - 1) / per;
+        variant = warps < 4LL * sms ? 2 : 1;
+    }
+    void (*kern)(LaunchArgs<float>) = !fast ? env_kernel_small<0>
+                                      : (variant == 2 ? env_kernel_small<2> : env_kernel_small<1>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

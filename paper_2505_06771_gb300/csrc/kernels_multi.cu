@@ -5,7 +5,7 @@
 // takes the next work item -- a run of envs of one class, one env per team -- from a device-wide
 // queue (one atomic counter), and runs those envs for all T steps.  Items are ordered largest
 // class first, so the longest jobs start first and the short ones fill the tail.
-#include "env_small.cuh"
+#include "env_nav4.cuh"
 #include "launch.h"
 
 namespace rl {
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(64) env_kernel_multi(MultiArgs M) {
                 const int tib = threadIdx.x / 4;
                 TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + tib;
                 if (tib < w.z) {
-                    if (fast) run_env_small<true>(M.a, tm, *S, list[tib]);
+                    if (fast) run_env_nav4(M.a, tm, *S, list[tib]);
                     else run_env_small<false>(M.a, tm, *S, list[tib]);
                 }
                 break;

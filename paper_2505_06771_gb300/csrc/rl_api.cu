@@ -35,7 +35,8 @@ static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
 
 struct Class {
     int nmax, lanes, begin, count, block_threads;
-    int warp_envs;  // envs per warp for the 4-robot binary32 kernels (0: full warps)
+    int warp_envs;  // envs per warp for the 4-robot binary32 kernels (0: default)
+    int variant;    // 4-robot binary32 Navigation fast path (0: by batch size)
 };
 
 }  // namespace
@@ -164,6 +165,7 @@ cudaError_t launch_class(const rl_env* h, const Class& c, rl::LaunchArgs<R> a, b
     a.env_list = h->d_lists + c.begin;
     a.n_list = c.count;
     a.warp_envs = c.warp_envs;
+    a.variant = c.variant;
     if constexpr (std::is_same<R, double>::value) {
         return rl::launch_f64(a, c.nmax, c.lanes, c.block_threads, max_blocks, h->st, reset);
     } else {
@@ -415,6 +417,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         k.lanes = lanes;
         k.block_threads = nm <= 16 ? 64 : 32;
         k.warp_envs = cfg->warp_envs > 0 ? std::min(32, cfg->warp_envs) : 0;
+        k.variant = (cfg->small_variant == 1 || cfg->small_variant == 2) ? cfg->small_variant : 0;
         if (cfg->block_threads > 0) {
             if (cfg->block_threads % 32 != 0 || cfg->block_threads > 256) { rl_destroy(h); return RL_ERR_ARG; }
             k.block_threads = std::max(cfg->block_threads, lanes);
@@ -562,6 +565,23 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     cudaError_t e = cudaMallocAsync(&saved, h->img_bytes, h->st);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(h, RL_ERR_OOM, "rl_tune: state copy"); }
     e = cudaMemcpyAsync(saved, h->d_img, h->img_bytes, cudaMemcpyDeviceToDevice, h->st);
+    // the probes write trajectories like a real rollout: kernels differ most in their stores
+    const size_t pob = (size_t)T_probe * h->total * h->obs_dim * h->esz;
+    const size_t prb = ((size_t)T_probe * h->E * h->esz + 255) & ~(size_t)255;
+    const size_t pdb = (size_t)T_probe * h->E;
+    void* probe_out = nullptr;
+    if (e == cudaSuccess) {
+        e = cudaMallocAsync(&probe_out, ((pob + 255) & ~(size_t)255) + prb + pdb, h->st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeAsync(saved, h->st);
+            return fail(h, RL_ERR_OOM, "rl_tune: probe trajectories");
+        }
+    }
+    char* po = (char*)probe_out;
+    void* p_obs = po;
+    void* p_rew = po + ((pob + 255) & ~(size_t)255);
+    uint8_t* p_done = (uint8_t*)(po + ((pob + 255) & ~(size_t)255) + prb);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -571,7 +591,7 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
             cudaError_t ee = cudaMemcpyAsync(h->d_img, saved, h->img_bytes, cudaMemcpyDeviceToDevice, h->st);
             if (ee != cudaSuccess) return cuda_fail(h, ee, "rl_tune");
             cudaEventRecord(e0, h->st);
-            rl_status st = rollout_enqueue(h, T_probe, nullptr, nullptr, nullptr);
+            rl_status st = rollout_enqueue(h, T_probe, p_obs, p_rew, p_done);
             if (st != RL_OK) return st;
             cudaEventRecord(e1, h->st);
             ee = cudaEventSynchronize(e1);
@@ -597,25 +617,36 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
         const unsigned ok = rl::supported_lanes(h->prec, all[c].nmax);
         float best = 1e30f;
         Class pick = all[c];
-        // candidates (lanes, block threads, envs per warp)
-        int cand[16][3];
+        // candidates (lanes, block threads, envs per warp, 4-robot kernel variant)
+        int cand[24][4];
         int nc_ = 0;
         if (h->prec == 32 && all[c].nmax == 4) {
             const int we4[4] = {1, 2, 4, 8}, we1[3] = {8, 16, 32};
-            for (int w = 0; w < 4; ++w) { cand[nc_][0] = 4; cand[nc_][1] = 128; cand[nc_][2] = we4[w]; ++nc_; }
-            for (int w = 0; w < 3; ++w) { cand[nc_][0] = 1; cand[nc_][1] = 4 * we1[w]; cand[nc_][2] = 0; ++nc_; }
-            cand[nc_][0] = 2; cand[nc_][1] = 64; cand[nc_][2] = 0; ++nc_;
+            for (int var = 1; var <= 2; ++var)
+                for (int w = 0; w < 4; ++w) {
+                    cand[nc_][0] = 4; cand[nc_][1] = 128; cand[nc_][2] = we4[w]; cand[nc_][3] = var;
+                    ++nc_;
+                }
+            for (int w = 0; w < 3; ++w) {
+                cand[nc_][0] = 1; cand[nc_][1] = 4 * we1[w]; cand[nc_][2] = 0; cand[nc_][3] = 0;
+                ++nc_;
+            }
+            cand[nc_][0] = 2; cand[nc_][1] = 64; cand[nc_][2] = 0; cand[nc_][3] = 0; ++nc_;
         } else {
             for (int lanes = 1; lanes <= 32; lanes <<= 1) {
                 if (!(ok & (unsigned)lanes)) continue;
                 for (int b = 0; b < 3; ++b)
-                    if (bts[b] >= lanes) { cand[nc_][0] = lanes; cand[nc_][1] = bts[b]; cand[nc_][2] = 0; ++nc_; }
+                    if (bts[b] >= lanes) {
+                        cand[nc_][0] = lanes; cand[nc_][1] = bts[b]; cand[nc_][2] = 0; cand[nc_][3] = 0;
+                        ++nc_;
+                    }
             }
         }
         for (int ci = 0; ci < nc_ && st == RL_OK; ++ci) {
             h->cls[0].lanes = cand[ci][0];
             h->cls[0].block_threads = cand[ci][1];
             h->cls[0].warp_envs = cand[ci][2];
+            h->cls[0].variant = cand[ci][3];
             float ms = 0.f;
             st = probe(ms);
             if (st == RL_OK && ms < best) { best = ms; pick = h->cls[0]; }
@@ -642,16 +673,18 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFreeAsync(saved, h->st);
+    if (probe_out) cudaFreeAsync(probe_out, h->st);
     drop_graph(h);
     if (st != RL_OK) return st;
     if (er != cudaSuccess) return cuda_fail(h, er, "rl_tune restore");
     if (h_choice) {
         h_choice[0] = h->use_multi;
         for (int c = 0; c < rl::kNumClasses; ++c) {
-            h_choice[1 + 4 * c] = c < h->ncls ? h->cls[c].nmax : 0;
-            h_choice[2 + 4 * c] = c < h->ncls ? h->cls[c].lanes : 0;
-            h_choice[3 + 4 * c] = c < h->ncls ? h->cls[c].block_threads : 0;
-            h_choice[4 + 4 * c] = c < h->ncls ? h->cls[c].warp_envs : 0;
+            h_choice[1 + 5 * c] = c < h->ncls ? h->cls[c].nmax : 0;
+            h_choice[2 + 5 * c] = c < h->ncls ? h->cls[c].lanes : 0;
+            h_choice[3 + 5 * c] = c < h->ncls ? h->cls[c].block_threads : 0;
+            h_choice[4 + 5 * c] = c < h->ncls ? h->cls[c].warp_envs : 0;
+            h_choice[5 + 5 * c] = c < h->ncls ? h->cls[c].variant : 0;
         }
     }
     return RL_OK;

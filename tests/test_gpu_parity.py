@@ -159,30 +159,40 @@ def test_teacher_forced_binary32(rl, case):
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
 
+FAST_KERNELS = dict(shuffle=dict(small_variant=1), gather=dict(small_variant=2),
+                    thread=dict(lanes=1))
+
+
+@pytest.mark.parametrize("kern", list(FAST_KERNELS))
 @pytest.mark.parametrize("N,E", [(4, 600), (3, 300), (2, 200)])
-def test_teacher_forced_thread_kernel(rl, N, E):
-    """The one-thread-per-env kernel (Navigation, scripted, no traces): poses, observations and
-    rewards against the oracle stepped from the same state.  A pose error within 1e-6 per step
-    bounds the filtered-control error by about 1e-6 / dt = 3e-5 and checks that every step used
-    the same barrier QP solution (an active-set mistake moves a robot by ~1e-4 m per step)."""
-    g, o = make_pair(0, N, episode_len=30)
+def test_teacher_forced_fast_kernels(rl, kern, N, E):
+    """The Navigation fast paths (scripted nominal control, no traces): the 4-lane team kernel
+    that reduces with shuffles, the one that publishes robot state in shared memory, and one
+    thread per env.  Poses, observations and rewards against the oracle stepped from the same
+    state.  A pose error within 1e-6 per step bounds the filtered-control error by about
+    1e-6 / dt = 3e-5 and checks that every step used the same barrier QP solution (an
+    active-set mistake moves a robot by ~1e-4 m per step)."""
+    g, o = make_pair(0, N, episode_len=30, **FAST_KERNELS[kern])
     err, _ = _teacher_forced(rl, g, o, [N] * E, 91, 40, traces=False)
-    print(f"\nthread kernel N={N}: max errors {err}")
+    print(f"\n{kern} kernel N={N}: max errors {err}")
     assert err["pose"] < 1e-6 and err["th"] < 2e-5
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
 
-@pytest.mark.parametrize("case", ["nav4", "nav4_thread", "nav3", "nav10", "nav4_f64"])
+@pytest.mark.parametrize("case", ["nav4", "nav4_shuffle", "nav4_gather", "nav4_thread", "nav3",
+                                  "nav10", "nav4_f64"])
 def test_teacher_forced_waypoints(rl, case):
     """Random Waypoint Navigation (goal reassigned on arrival): every kernel that runs 4-robot,
     3-robot, 10-robot and binary64 Navigation against the oracle stepped from the same state.
     The arrival radius is large so that arrivals happen within the 40 steps; goals, arrival
     counts and done flags are compared exactly."""
-    N = {"nav4": 4, "nav4_thread": 4, "nav3": 3, "nav10": 10, "nav4_f64": 4}[case]
+    N = 10 if case == "nav10" else (3 if case == "nav3" else 4)
     prec = 64 if case == "nav4_f64" else 32
-    g, o = make_pair(0, N, prec, goal_eps=0.35, episode_len=10_000)
+    kern = case.split("_")[1] if case in ("nav4_shuffle", "nav4_gather", "nav4_thread") else None
+    g, o = make_pair(0, N, prec, goal_eps=0.35, episode_len=10_000,
+                     **(FAST_KERNELS[kern] if kern else {}))
     E = 96 if N == 10 else 300
-    err, _ = _teacher_forced(rl, g, o, [N] * E, 23, 40, traces=(case != "nav4_thread"))
+    err, _ = _teacher_forced(rl, g, o, [N] * E, 23, 40, traces=kern is None)
     print(f"\nwaypoints {case}: max errors {err}")
     tol = 1e-5 if prec == 64 else 1.0
     assert err["pose"] < 1e-6 * tol and err["rew"] < 1e-5 * tol and err["obs"] < 1e-5 * tol
