@@ -104,14 +104,14 @@ __device__ __forceinline__ void nav4_pair(int s, int N, int& a, int& b) {
 
 // The whole QP in registers (qp_regs.cuh), out of line: reached by the few QPs with a second
 // violated row after the closed-form step.  Operands come from the team's published values.
-static __device__ __noinline__ QPResult nav4_full(const TeamSmem<float, 4>& S, int N,
+static __device__ __noinline__ QPResult nav4_full(const TeamSmem<float, 4>& S, int cb, int N,
                                                   const QPConsts<float> c, bool& overflow,
                                                   float& usx, float& usy, int i) {
     float px[4], py[4], u0[8], u[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        px[j] = S.g4[j][0].w;
-        py[j] = S.g4[j][1].x;
+        px[j] = S.g4[cb][j][0].w;
+        py[j] = S.g4[cb][j][1].x;
         u0[2 * j] = S.g2[j].x;
         u0[2 * j + 1] = S.g2[j].y;
     }
@@ -157,22 +157,33 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) jo[sl] = sl + (sl >= i ? 1 : 0);
 
-    // Every lane publishes its robot's pose and projected point (g4[i][0] = x, y, th, p_x;
-    // g4[i][1] = p_y, reward term, out-of-arena flag, arrival flag) once per step, and its
-    // nominal velocity (g2[i]) once per QP.  __syncwarp over the team before a write (every
-    // lane is done reading the previous values) and after it (the values are visible).
+    // Every lane publishes its robot's pose and projected point (g4[cb][i][0] = x, y, th, p_x;
+    // g4[cb][i][1] = p_y, reward term, out-of-arena flag, arrival flag) once per step, and its
+    // nominal velocity (g2[i]) once per QP, each write followed by a __syncwarp over the team.
+    // The state alternates between two buffers, so every write is separated from the last
+    // reads of the values it replaces by the other publication's __syncwarp.
+    int cb = 1;
     auto publish = [&](float npx, float npy, float dterm, int oob_i, int arr_i) {
-        tm.sync();
-        S.g4[i][0] = make_float4(x, y, th, npx);
-        S.g4[i][1] = make_float4(npy, dterm, (float)oob_i, (float)arr_i);
+        cb ^= 1;
+        S.g4[cb][i][0] = make_float4(x, y, th, npx);
+        S.g4[cb][i][1] = make_float4(npy, dterm, (float)oob_i, (float)arr_i);
         tm.sync();
     };
     float npx = x + k.l * cs, npy = y + k.l * sn;
     publish(npx, npy, 0.f, 0, 0);
 
+    // Noise words of the own robot for the coming step, drawn one step ahead (the draw
+    // depends on the counters only, so it overlaps the previous step's work).  Robots 2m and
+    // 2m+1 share the Philox block (pair m, step t); both lanes draw it and keep their words.
+    auto noise_words = [&](uint32_t& nwx, uint32_t& nwy) {
+        const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)t);
+        nwx = (i & 1) ? w.w[2] : w.w[0];
+        nwy = (i & 1) ? w.w[3] : w.w[1];
+    };
+    uint32_t nwx, nwy;
+    noise_words(nwx, nwy);
+
     float ret_acc = 0.f;
-    int nz_t = -2, nz_ep = -1;   // noise words cached for step nz_t + 1 of episode nz_ep
-    uint32_t nz_nx = 0u, nz_ny = 0u;
 
     for (int step = 0; step < A.T; ++step) {
         // ---- nominal SI velocity of the own robot (go to goal, cap, noise, cap)
@@ -181,42 +192,21 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
         float ux = k.k_si * (gx - px), uy = k.k_si * (gy - py);
         cap_fast(ux, uy, k.vmax);
         {
-            // Noise words of this robot for step t.  Robots 2m and 2m+1 share the Philox block
-            // (pair m, step t); their two lanes compute the blocks of steps t and t+1 at once
-            // and swap them, so each lane runs Philox every other step.
-            uint32_t wx, wy;
-            if (nz_ep == ep && nz_t + 1 == t) {
-                wx = nz_nx;
-                wy = nz_ny;
-                nz_t = -2;
-            } else {
-                const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)(t + (i & 1)));
-                uint32_t o[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) o[m] = __shfl_xor_sync(tm.mask, w.w[m], 1, 4);
-                wx = (i & 1) ? o[2] : w.w[0];
-                wy = (i & 1) ? o[3] : w.w[1];
-                nz_nx = (i & 1) ? w.w[2] : o[0];
-                nz_ny = (i & 1) ? w.w[3] : o[1];
-                nz_t = t;
-                nz_ep = ep;
-            }
-            const float ex = __fmul_rn(__fsub_rn(unit24(wx), 0.5f), k.noise_scale);
-            const float ey = __fmul_rn(__fsub_rn(unit24(wy), 0.5f), k.noise_scale);
+            const float ex = __fmul_rn(__fsub_rn(unit24(nwx), 0.5f), k.noise_scale);
+            const float ey = __fmul_rn(__fsub_rn(unit24(nwy), 0.5f), k.noise_scale);
             ux += k.noise_on ? ex : 0.f;
             uy += k.noise_on ? ey : 0.f;
         }
         cap_fast(ux, uy, k.vmax);
 
         // ---- the barrier QP: own rows, partners' projected points and u_nom, team maximum
-        tm.sync();
         S.g2[i] = make_float2(ux, uy);
         tm.sync();
         float qx[2], qy[2], wx[2], wy[2];
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
-            qx[d] = S.g4[jn[d]][0].w;
-            qy[d] = S.g4[jn[d]][1].x;
+            qx[d] = S.g4[cb][jn[d]][0].w;
+            qy[d] = S.g4[cb][jn[d]][1].x;
             const float2 w = S.g2[jn[d]];
             wx[d] = w.x;
             wy[d] = w.y;
@@ -238,7 +228,8 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
             float cx, cy, bv, h = 1e30f;
             if (s1 < P) {
                 nav4_pair(s1, N, a, b);
-                const float dx = S.g4[a][0].w - S.g4[b][0].w, dy = S.g4[a][1].x - S.g4[b][1].x;
+                const float dx = S.g4[cb][a][0].w - S.g4[cb][b][0].w;
+                const float dy = S.g4[cb][a][1].x - S.g4[cb][b][1].x;
                 h = dx * dx + dy * dy - qc.r2;
                 bv = qc.gamma * h * h * h;
                 cx = -2.f * dx;
@@ -246,7 +237,7 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
             } else {
                 const int m = s1 - P, sd = m & 3;
                 a = m >> 2;
-                const float pa = (sd < 2) ? S.g4[a][0].w : S.g4[a][1].x;
+                const float pa = (sd < 2) ? S.g4[cb][a][0].w : S.g4[cb][a][1].x;
                 const float dd = (sd == 0) ? qc.xmax - qc.half_r - pa
                                : (sd == 1) ? pa - qc.xmin - qc.half_r
                                : (sd == 2) ? qc.ymax - qc.half_r - pa
@@ -277,7 +268,7 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
             if (K != 0u) {
                 // a second violated row: the whole QP again, in registers
                 bool overflow;
-                res = nav4_full(S, N, qc, overflow, usx, usy, i);
+                res = nav4_full(S, cb, N, qc, overflow, usx, usy, i);
                 if (overflow) {
                     res = small_general(tm, S, N, px, py, ux, uy, qc);
                     usx = own ? S.qp.s.f.ux[i] : 0.f;
@@ -323,8 +314,8 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
         float4 oa[3], ob[3];
 #pragma unroll
         for (int sl = 0; sl < 3; ++sl) {
-            oa[sl] = S.g4[jo[sl]][0];
-            ob[sl] = S.g4[jo[sl]][1];
+            oa[sl] = S.g4[cb][jo[sl]][0];
+            ob[sl] = S.g4[cb][jo[sl]][1];
         }
         int col = 0, oob = oob_i, narr = arr_i;
         float rew = own ? dterm : 0.f;
@@ -377,11 +368,15 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
             __sincosf(th, &sn, &cs);
             npx = x + k.l * cs;
             npy = y + k.l * sn;
+            // republish into the current buffer once every lane is done reading it
             tm.sync();
-            publish(npx, npy, 0.f, 0, 0);
+            S.g4[cb][i][0] = make_float4(x, y, th, npx);
+            S.g4[cb][i][1] = make_float4(npy, 0.f, 0.f, 0.f);
+            tm.sync();
 #pragma unroll
-            for (int sl = 0; sl < 3; ++sl) oa[sl] = S.g4[jo[sl]][0];
+            for (int sl = 0; sl < 3; ++sl) oa[sl] = S.g4[cb][jo[sl]][0];
         }
+        noise_words(nwx, nwy);
 
         // ---- observations of the own robot: [x, y, th, gx, gy], then the others in index
         // order relative to it

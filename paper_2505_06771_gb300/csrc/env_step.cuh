@@ -208,8 +208,8 @@ union QPUnion {
 
 template <typename R, int NMAX>
 struct TeamSmem {
-    float4 g4[4][2];     // 4-robot Navigation kernel: per-robot state published each step
-    float2 g2[4];        // and nominal velocities
+    float4 g4[2][4][2];  // 4-robot Navigation kernel: per-robot state published each step
+    float2 g2[4];        // (two buffers, alternating) and nominal velocities
     QPUnion<NMAX> qp;
     R sx[NMAX], sy[NMAX], sth[NMAX];
     int slevel[NMAX];
