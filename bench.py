@@ -58,6 +58,14 @@ WORKLOADS = {
 }
 
 
+# the kernel each workload's rollout launches (one launch per bench step)
+KERNELS = {"nav": "rl::env_kernel_small<1> (4-robot shuffle team kernel)",
+           "waypoint": "rl::env_kernel_small<2> (4-robot gather team kernel)",
+           "uneven": "rl::env_kernel_multi (one persistent launch over all size classes)",
+           "largen": "rl::env_kernel<float, 32, 20> (20-robot class, explicit-inverse QP)",
+           "tiny": "rl::env_kernel<double, 4, 4> (binary64 team kernel)"}
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -368,7 +376,7 @@ def run_rollout(a):
     peak, peak_src = _peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": _ncu_traffic(a.workload),
-            "peak_source": peak_src, "kernel": "rl::env_kernel_small / env_kernel_multi",
+            "peak_source": peak_src, "kernel": KERNELS.get(a.workload, "rl::env_kernel"),
             "algorithmic_bytes_per_launch": alg_bytes,
             "bytes_per_env_step": alg_bytes / (E * T)}
 

@@ -16,18 +16,16 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     const int tpb = block_threads / 4;
     const size_t smem = (size_t)tpb * sizeof(TeamSmem<float, 4>);
     const bool fast = is_fast(a);
-    const int per = (a.warp_envs >= 1 && a.warp_envs <= 8) ? a.warp_envs : 4;
     int variant = a.variant;
     if (fast && variant != 1 && variant != 2) {
-        // auto: the gather kernel while the batch leaves schedulers idle (its latency per step
-        // is lower), the shuffle kernel once there are more warps than schedulers
-        int dev = 0, sms = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        const long long warps = ((long long)a.n_list + per - 1) / per;
-        variant = warps < 4LL * sms ? 2 : 1;
+        // auto: the gather kernel (lower latency per step) for small batches, the shuffle
+        // kernel (fewer instructions per env-step) for large ones; measured on GB300, 4096
+        // envs run 10% faster with the shuffle kernel, one env 20% faster with the gather one
+        variant = a.n_list <= 1024 ? 2 : 1;
     }
+    // envs per warp: 8 for the shuffle kernel (fastest on 4096 envs), 4 otherwise
+    const int per = (a.warp_envs >= 1 && a.warp_envs <= 8) ? a.warp_envs
+                                                             : ((fast && variant == 1) ? 8 : 4);
     void (*kern)(LaunchArgs<float>) = !fast ? env_kernel_small<0>
                                       : (variant == 2 ? env_kernel_small<2> : env_kernel_small<1>);
     if (smem > 48 * 1024) {
@@ -39,7 +37,9 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     int blocks = (a.n_list + envs_per_block - 1) / envs_per_block;
     if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     if (blocks <= 0) return cudaSuccess;
-    kern<<<blocks, block_threads, smem, st>>>(a);
+    LaunchArgs<float> b = a;
+    b.warp_envs = per;  // the kernel walks the envs with the same stride
+    kern<<<blocks, block_threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
