@@ -55,6 +55,15 @@ WORKLOADS = {
                      context={"paper_table2_ms_per_10k_steps": 9.18,
                               "paper_hardware": "JAX on an Apple M4 Pro CPU (position "
                                                 "controller); another machine: context only"}),
+    "waypoint_pose": dict(desc="random waypoint navigation under the unicycle pose controller: 1 "
+                               "env x 4 robots x 10000 steps, a new goal pose on arrival within "
+                               "0.05 m, fp32 (Table 2's pose-controller row)",
+                          scenario=0, E=1, N=4, T=10000, precision=32, near=0.0, n_max=4,
+                          goal_eps=0.05, episode_len=10000, controller=1,
+                          context={"paper_table2_ms_per_10k_steps": 11.42,
+                                   "paper_hardware": "JAX on an Apple M4 Pro CPU (pose "
+                                                     "controller); another machine: context "
+                                                     "only"}),
 }
 
 
@@ -63,7 +72,8 @@ KERNELS = {"nav": "rl::env_kernel_small<1> (4-robot shuffle team kernel)",
            "waypoint": "rl::env_kernel_small<2> (4-robot gather team kernel)",
            "uneven": "rl::env_kernel_multi (one persistent launch over all size classes)",
            "largen": "rl::env_kernel<float, 32, 20> (20-robot class, explicit-inverse QP)",
-           "tiny": "rl::env_kernel<double, 4, 4> (binary64 team kernel)"}
+           "tiny": "rl::env_kernel<double, 4, 4> (binary64 team kernel)",
+           "waypoint_pose": "rl::env_kernel_small<2> (4-robot gather team kernel, pose controller)"}
 
 
 def _args():
@@ -184,7 +194,7 @@ def _robots(w):
 
 def _cfg_overrides(w):
     return dict(n_max=w["n_max"], near_frac=w["near"], goal_eps=w.get("goal_eps", 0.0),
-                episode_len=w.get("episode_len", 100))
+                episode_len=w.get("episode_len", 100), controller=w.get("controller", 0))
 
 
 def _oracle_cfg(w):
@@ -279,7 +289,7 @@ def _teacher_forced_error(rl, w, steps=8, envs=64):
     for _ in range(steps):
         st = env.state_arrays()
         s = oracle.State(c, st["n_robots"])
-        for k in ("x", "y", "th", "gx", "gy"):
+        for k in ("x", "y", "th", "gx", "gy", "gth"):
             getattr(s, k)[:] = st[k]
         s.level[:] = st["level"]
         s.t[:] = st["t"]

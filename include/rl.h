@@ -55,6 +55,8 @@ typedef enum {
 } rl_status;
 
 typedef enum { RL_SCEN_NAVIGATION = 0, RL_SCEN_FORAGING = 1 } rl_scenario;
+typedef enum { RL_CTRL_POSITION = 0, RL_CTRL_POSE = 1 } rl_controller;
+
 typedef enum { RL_PREC_F32 = 32, RL_PREC_F64 = 64 } rl_precision;
 
 /* Counters per env (int32, cumulative since rl_create / rl_reset). */
@@ -90,6 +92,9 @@ typedef struct {
                                kernel that reduces across lanes with shuffles (faster on large
                                batches), 2 the team kernel that publishes each robot's state in
                                shared memory (lower latency per step); 0 picks by batch size */
+    int32_t controller;     /* Navigation scripted nominal control: RL_CTRL_POSITION (go to the
+                               goal point, k_si) or RL_CTRL_POSE (unicycle posture regulation to
+                               the goal pose: position and goal heading, pose_k1..3) */
     double gamma;           /* barrier gain (100) */
     double r;               /* safety radius [m] (0.17) */
     double l;               /* projection distance [m] (0.05) */
@@ -110,6 +115,8 @@ typedef struct {
     double goal_eps;        /* Navigation: > 0 gives a robot a new goal when its projected point
                                ends a step within goal_eps of its goal (Random Waypoint
                                Navigation, Sec. 4.2); 0 (default) keeps goals for the episode */
+    double pose_k1, pose_k2, pose_k3;  /* pose controller gains: approach, heading, final
+                                          orientation weight (1, 2, 1), all > 0 */
 } rl_config;
 
 /* Optional outputs of one step (any pointer may be NULL). */

@@ -53,11 +53,12 @@ def build(force: bool = False) -> str:
 class Cfg(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("scenario", "scripted", "episode_len", "n_res_min", "n_res_max", "max_attempts",
-                 "n_max", "r_max")] + \
+                 "n_max", "r_max", "controller")] + \
                [(n, ctypes.c_double) for n in
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
-                 "near_frac", "near_dmin", "near_dmax", "goal_eps")]
+                 "near_frac", "near_dmin", "near_dmax", "goal_eps", "pose_k1", "pose_k2",
+                 "pose_k3")]
 
 
 _P = ctypes.POINTER
@@ -66,7 +67,7 @@ _D, _I, _U8 = ctypes.c_double, ctypes.c_int32, ctypes.c_uint8
 
 class _Batch(ctypes.Structure):
     _fields_ = [("x", _P(_D)), ("y", _P(_D)), ("th", _P(_D)), ("gx", _P(_D)), ("gy", _P(_D)),
-                ("level", _P(_I)), ("t", _P(_I)), ("ep", _P(_I)), ("n_res", _P(_I)),
+                ("gth", _P(_D)), ("level", _P(_I)), ("t", _P(_I)), ("ep", _P(_I)), ("n_res", _P(_I)),
                 ("qx", _P(_D)), ("qy", _P(_D)), ("qlevel", _P(_I)), ("qactive", _P(_I)),
                 ("counters", _P(_I))]
 
@@ -114,7 +115,8 @@ def default_cfg(scenario: int = NAV, n_max: int = 4, **overrides) -> dict:
              gamma=100.0, r=0.17, l=0.05, vmax=0.2, wmax=3.6, dt=0.033, kappa=0.4, k_si=1.0,
              noise_amp=0.05, c_col=1.0 if scenario == NAV else 0.0, forage_radius=0.25,
              xmin=-1.6, xmax=1.6, ymin=-1.0, ymax=1.0, init_margin=0.2, min_sep=0.3,
-             near_frac=0.0, near_dmin=0.18, near_dmax=0.20, goal_eps=0.0)
+             near_frac=0.0, near_dmin=0.18, near_dmax=0.20, goal_eps=0.0, controller=0,
+             pose_k1=1.0, pose_k2=2.0, pose_k3=1.0)
     c.update(overrides)
     return c
 
@@ -146,7 +148,7 @@ class State:
         R = max(int(c["r_max"]), 1)
         self.r_max = int(c["r_max"])
         self.off = np.concatenate([[0], np.cumsum(self.n_robots)]).astype(np.int64)
-        for name in ("x", "y", "th", "gx", "gy"):
+        for name in ("x", "y", "th", "gx", "gy", "gth"):
             setattr(self, name, np.zeros(tot, np.float64))
         self.level = np.zeros(tot, np.int32)
         self.t = np.zeros(E, np.int32)
@@ -166,7 +168,7 @@ class State:
 
     def _c(self) -> _Batch:
         b = _Batch()
-        for name in ("x", "y", "th", "gx", "gy", "qx", "qy"):
+        for name in ("x", "y", "th", "gx", "gy", "gth", "qx", "qy"):
             setattr(b, name, _ptr(getattr(self, name), _D))
         for name in ("level", "t", "ep", "n_res", "qlevel", "qactive", "counters"):
             setattr(b, name, _ptr(getattr(self, name), _I))
@@ -242,6 +244,15 @@ def qp_project(A, b, u0):
     st = _lib().orc_qp_project(n, m, _ptr(A, _D), _ptr(b, _D), _ptr(u0, _D), _ptr(u, _D),
                                _ptr(lam, _D), ctypes.byref(q), ctypes.byref(it))
     return u, lam, int(st), int(q.value), int(it.value)
+
+
+def pose_control(c: dict, pose, goal):
+    """Nominal unicycle command (v, omega) of the pose controller from pose and goal [x, y, th]."""
+    p = np.ascontiguousarray(pose, dtype=np.float64)
+    g = np.ascontiguousarray(goal, dtype=np.float64)
+    vw = np.zeros(2)
+    _lib().orc_pose_control(ctypes.byref(_cfg(c)), _ptr(p, _D), _ptr(g, _D), _ptr(vw, _D))
+    return vw
 
 
 def cbf_rows(c: dict, px, py):

@@ -99,7 +99,7 @@ int orc_obs_dim(const orc_cfg* c) {
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
     int n, t, ep, n_res;
-    double x[ORC_NMAX], y[ORC_NMAX], th[ORC_NMAX], gx[ORC_NMAX], gy[ORC_NMAX];
+    double x[ORC_NMAX], y[ORC_NMAX], th[ORC_NMAX], gx[ORC_NMAX], gy[ORC_NMAX], gth[ORC_NMAX];
     int32_t level[ORC_NMAX];
     double qx[ORC_RMAX], qy[ORC_RMAX];
     int32_t qlevel[ORC_RMAX], qactive[ORC_RMAX];
@@ -113,6 +113,7 @@ static void load_env(const orc_cfg* c, const orc_batch* b, int e, int off, int n
     for (int i = 0; i < n; ++i) {
         s->x[i] = b->x[off + i]; s->y[i] = b->y[off + i]; s->th[i] = b->th[off + i];
         s->gx[i] = b->gx[off + i]; s->gy[i] = b->gy[off + i]; s->level[i] = b->level[off + i];
+        s->gth[i] = b->gth[off + i];
     }
     for (int k = 0; k < c->r_max; ++k) {
         s->qx[k] = b->qx[e * c->r_max + k]; s->qy[k] = b->qy[e * c->r_max + k];
@@ -127,6 +128,7 @@ static void store_env(const orc_cfg* c, orc_batch* b, int e, int off, const env_
     for (int i = 0; i < s->n; ++i) {
         b->x[off + i] = s->x[i]; b->y[off + i] = s->y[i]; b->th[off + i] = s->th[i];
         b->gx[off + i] = s->gx[i]; b->gy[off + i] = s->gy[i]; b->level[off + i] = s->level[i];
+        b->gth[off + i] = s->gth[i];
     }
     for (int k = 0; k < c->r_max; ++k) {
         b->qx[e * c->r_max + k] = s->qx[k]; b->qy[e * c->r_max + k] = s->qy[k];
@@ -214,6 +216,7 @@ static void sample_env(const orc_cfg* c, uint64_t seed, int e, int ep, int n, en
         draw(seed, e, ep, P_GOAL, i, 0, w);
         s->gx[i] = (double)(lox + u01(w[0]) * wx);
         s->gy[i] = (double)(loy + u01(w[1]) * wy);
+        s->gth[i] = (double)(-pif + u01(w[2]) * twopif);  /* goal heading (pose controller) */
         s->level[i] = 0;
     }
     s->n_res = 0;
@@ -437,6 +440,33 @@ int orc_build_cbf_rows(const orc_cfg* c, int N, const double* px, const double* 
 
 static double wrap_angle(double a) { return atan2(sin(a), cos(a)); }
 
+/* Posture regulation of a unicycle in polar coordinates (Aicardi, Casalino, Bicchi, Balestrino,
+   "Closed loop steering of unicycle-like vehicles via Lyapunov techniques", IEEE Robotics &
+   Automation Magazine 1995).  In the goal's frame the robot sits at (xr, yr) with heading thr;
+   rho is its distance to the goal, gam the angle from its heading to the direction of the goal,
+   del the angle of that direction in the goal's frame.  The law
+       v = k1 rho cos(gam),  omega = k2 gam + k1 (sin(gam) cos(gam) / gam) (gam + k3 del)
+   makes V = (rho^2 + gam^2 + k3 del^2) / 2 non-increasing: dV/dt = -k1 cos^2(gam) rho^2 - k2 gam^2.
+   The paper evaluates a unicycle pose controller (Sec. 4.2, Table 2) without giving its law;
+   this published one stands for it (a reading). */
+void orc_pose_control(const orc_cfg* c, const double* pose, const double* goal, double* vw) {
+    const double cg = cos(goal[2]), sg = sin(goal[2]);
+    const double dx = pose[0] - goal[0], dy = pose[1] - goal[1];
+    const double xr = cg * dx + sg * dy, yr = -sg * dx + cg * dy;
+    const double thr = wrap_angle(pose[2] - goal[2]);
+    const double rho = hypot(xr, yr);
+    if (rho == 0.0) {  /* on the goal point: turn in place towards the goal heading */
+        vw[0] = 0.0;
+        vw[1] = -c->pose_k2 * thr;
+        return;
+    }
+    const double gam = wrap_angle(atan2(yr, xr) + M_PI - thr);
+    const double del = wrap_angle(gam + thr);
+    const double sinc = (gam == 0.0) ? 1.0 : sin(gam) / gam;
+    vw[0] = c->pose_k1 * rho * cos(gam);
+    vw[1] = c->pose_k2 * gam + c->pose_k1 * sinc * cos(gam) * (gam + c->pose_k3 * del);
+}
+
 void orc_unicycle_update(const orc_cfg* c, double ux, double uy, double* pose, double* vw) {
     double cs = cos(pose[2]), sn = sin(pose[2]);
     /* SI -> unicycle map for the point l ahead of the wheel axle */
@@ -554,8 +584,19 @@ static void env_step(const orc_cfg* c, uint64_t seed, int e, env_t* s, const dou
                 if (best >= 0) { tx = s->qx[best]; ty = s->qy[best]; }
                 else { tx = px[i]; ty = py[i]; }
             }
-            ux = c->k_si * (tx - px[i]);
-            uy = c->k_si * (ty - py[i]);
+            if (c->scenario == ORC_NAV && c->controller == ORC_CTRL_POSE) {
+                /* unicycle pose controller, then its command as the projected point's velocity
+                   (the SI <-> unicycle map at distance l, c2) */
+                const double pose[3] = {s->x[i], s->y[i], s->th[i]};
+                const double goal[3] = {s->gx[i], s->gy[i], s->gth[i]};
+                double vw[2];
+                orc_pose_control(c, pose, goal, vw);
+                ux = vw[0] * cs[i] - c->l * vw[1] * sn[i];
+                uy = vw[0] * sn[i] + c->l * vw[1] * cs[i];
+            } else {
+                ux = c->k_si * (tx - px[i]);
+                uy = c->k_si * (ty - py[i]);
+            }
             cap_norm(&ux, &uy, c->vmax);
             if (c->noise_amp > 0.0) {
                 uint32_t w[4];
@@ -671,6 +712,7 @@ static void env_step(const orc_cfg* c, uint64_t seed, int e, env_t* s, const dou
                     draw(seed, e, s->ep, P_GOAL, i, (uint32_t)(s->t + 1), w);
                     s->gx[i] = (double)(lox + u01(w[0]) * wx);
                     s->gy[i] = (double)(loy + u01(w[1]) * wy);
+                    s->gth[i] = (double)(-(float)M_PI + u01(w[2]) * (float)(2.0 * M_PI));
                     cnt[ORC_CNT_SUCCESS] += 1;
                 }
             }
@@ -705,6 +747,10 @@ static int check_cfg(const orc_cfg* c, int E, const int32_t* n_robots) {
                                       c->n_res_min > c->n_res_max))
         return 1;
     if (!(c->goal_eps >= 0.0) || (c->goal_eps > 0.0 && c->scenario != ORC_NAV)) return 1;
+    if (c->controller != ORC_CTRL_POSITION && c->controller != ORC_CTRL_POSE) return 1;
+    if (c->controller == ORC_CTRL_POSE &&
+        (c->scenario != ORC_NAV || !(c->pose_k1 > 0.0) || !(c->pose_k2 > 0.0) || !(c->pose_k3 > 0.0)))
+        return 1;
     for (int e = 0; e < E; ++e)
         if (n_robots[e] < 1 || n_robots[e] > c->n_max) return 1;
     return 0;

@@ -21,6 +21,7 @@
 #define ORC_NCOUNT 8  /* int32 counters per environment */
 
 enum { ORC_NAV = 0, ORC_FORAGE = 1 };
+enum { ORC_CTRL_POSITION = 0, ORC_CTRL_POSE = 1 };
 enum { ORC_CNT_COLLISIONS = 0, ORC_CNT_OOB = 1, ORC_CNT_SUCCESS = 2, ORC_CNT_QP_ACTIVE = 3,
        ORC_CNT_QP_FLAGGED = 4, ORC_CNT_QP_INFEASIBLE = 5, ORC_CNT_EPISODES = 6,
        ORC_CNT_QP_ITERS = 7 };
@@ -32,16 +33,20 @@ typedef struct {
     int32_t n_res_min, n_res_max;   /* foraging resources per episode */
     int32_t max_attempts;  /* rejection-sampling attempts per robot */
     int32_t n_max, r_max;  /* observation padding (robots, resources) */
+    int32_t controller;    /* Navigation scripted control: ORC_CTRL_POSITION or ORC_CTRL_POSE */
     double gamma, r, l, vmax, wmax, dt, kappa, k_si, noise_amp, c_col, forage_radius;
     double xmin, xmax, ymin, ymax, init_margin, min_sep;
     double near_frac, near_dmin, near_dmax;
     double goal_eps;       /* Navigation: > 0 assigns a new goal on arrival (Random Waypoint
                               Navigation, Sec. 4.2); 0 keeps the goals for the episode */
+    double pose_k1, pose_k2, pose_k3;  /* pose controller gains (approach, heading, final
+                                          orientation weight), all > 0 */
 } orc_cfg;
 
 /* Batched structure-of-arrays state.  Robots of env e occupy [off_e, off_e + n_e). */
 typedef struct {
     double *x, *y, *th, *gx, *gy;     /* [sum n] */
+    double *gth;                      /* [sum n] goal heading (pose controller) */
     int32_t *level;                   /* [sum n] foraging level */
     int32_t *t, *ep, *n_res;          /* [E] */
     double *qx, *qy;                  /* [E * r_max] */
@@ -83,6 +88,10 @@ int orc_qp_project(int n, int m, const double* A, const double* bvec, const doub
 /* Barrier-certificate QP rows of one env from its projected points: m = N(N-1)/2 + 4N rows. */
 int orc_build_cbf_rows(const orc_cfg* c, int N, const double* px, const double* py,
                        double* A, double* bvec);
+
+/* Unicycle pose controller (posture regulation in polar coordinates, Aicardi et al. 1995):
+   the nominal (v, omega) driving pose [x, y, th] to goal [gx, gy, gth]. */
+void orc_pose_control(const orc_cfg* c, const double* pose, const double* goal, double* vw);
 
 /* Single-integrator velocity -> unicycle command -> wheel clip -> Euler step, one robot.
    pose: in/out [x, y, th]; vw: out [v, omega] after the clip. */

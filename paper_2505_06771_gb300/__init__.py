@@ -41,11 +41,12 @@ class RLConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("scenario", "precision", "scripted", "episode_len", "n_res_min", "n_res_max",
                  "r_max", "n_max", "max_attempts", "qp_max_iter", "resolve_f64", "lanes",
-                 "block_threads", "warp_envs", "small_variant")] + \
+                 "block_threads", "warp_envs", "small_variant", "controller")] + \
                [(n, ctypes.c_double) for n in
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
-                 "near_frac", "near_dmin", "near_dmax", "h_flag", "goal_eps")]
+                 "near_frac", "near_dmin", "near_dmax", "h_flag", "goal_eps", "pose_k1",
+                 "pose_k2", "pose_k3")]
 
 
 class RLRequest(ctypes.Structure):
@@ -395,13 +396,13 @@ def noalloc_state_bytes(cfg: dict, n_envs: int, n_robots: int) -> int:
 _SEGS = [("x", "r", "T"), ("y", "r", "T"), ("th", "r", "T"), ("gx", "r", "T"), ("gy", "r", "T"),
          ("level", "i", "T"), ("t", "i", "E"), ("ep", "i", "E"), ("n_res", "i", "E"),
          ("qx", "r", "RM"), ("qy", "r", "RM"), ("qlevel", "i", "RM"), ("qactive", "i", "RM"),
-         ("counters", "i", "C"), ("n_robots", "i", "E"), ("off", "i", "E1")]
+         ("counters", "i", "C"), ("n_robots", "i", "E"), ("off", "i", "E1"), ("gth", "r", "T")]
 
 
 def parse_state(blob: bytes) -> dict:
     hdr = np.frombuffer(blob, np.int32, 10)
     magic, version, prec, scen, E, T, rmax, nmax = [int(v) for v in hdr[:8]]
-    if magic != 0x31534C52 or version != 1:
+    if magic != 0x31534C52 or version != 2:
         raise ValueError("not a state blob")
     seed, img = np.frombuffer(blob, np.uint64, 2, offset=32)
     rdt = np.float64 if prec == 64 else np.float32

@@ -1,7 +1,8 @@
 // env_nav4.cuh -- the Navigation step for envs of at most 4 robots (binary32, scripted nominal
 // control, no traces): the hot path of the 4096 x 4 rollout and of the single-env waypoint run.
 //
-// Same method and results (up to rounding) as run_env_small.  A team of 4 lanes runs one env,
+// Same method and results (up to rounding) as run_env_small, for either scripted controller
+// (position, or the unicycle pose controller).  A team of 4 lanes runs one env,
 // lane i owning robot i, and the step is organised around two all-gathers -- one batch of
 // independent shuffles each, so the team pays one shuffle latency per batch:
 //   1. after the nominal velocities are formed, every lane gathers all four (u_nom);
@@ -138,7 +139,7 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
     qc.tol_abs = 2e-7f; qc.tol_rel = 1e-6f; qc.eps_dep = 1e-5f; qc.tol_lam = 1e-6f;
 
     float x = A.s.x[row], y = A.s.y[row], th = A.s.th[row];
-    float gx = A.s.gx[row], gy = A.s.gy[row];
+    float gx = A.s.gx[row], gy = A.s.gy[row], gth = A.s.gth[row];
     const int lv = A.s.level[row];
     float sn, cs;
     __sincosf(th, &sn, &cs);
@@ -189,7 +190,13 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
         // ---- nominal SI velocity of the own robot (go to goal, cap, noise, cap)
         const float px = npx, py = npy;
         const float dold = fast_norm(px - gx, py - gy);
-        float ux = k.k_si * (gx - px), uy = k.k_si * (gy - py);
+        float ux, uy;
+        if (k.controller == 1) {
+            pose_nominal<float>(k, x, y, th, gx, gy, gth, ux, uy);
+        } else {
+            ux = k.k_si * (gx - px);
+            uy = k.k_si * (gy - py);
+        }
         cap_fast(ux, uy, k.vmax);
         {
             const float ex = __fmul_rn(__fsub_rn(unit24(nwx), 0.5f), k.noise_scale);
@@ -340,10 +347,10 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
         rew -= k.c_col * (float)col;
         if (arr_i) {
             // Random Waypoint Navigation: a new goal for the robot that arrived
-            const float2 g = waypoint_goal(A.seed, A.sc.lox, A.sc.loy, A.sc.wx, A.sc.wy, e, ep,
-                                           i, t + 1);
+            const float3 g = waypoint_goal(A.sc, A.seed, e, ep, i, t + 1);
             gx = g.x;
             gy = g.y;
+            gth = g.z;
         }
         c_col += col;
         c_oob += oob;
@@ -363,7 +370,7 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
             small_reset(tm, S, A, e, ep, N);
             if (own) {
                 x = S.fx[i]; y = S.fy[i]; th = S.fth[i];
-                gx = S.sx[i]; gy = S.sy[i];
+                gx = S.sx[i]; gy = S.sy[i]; gth = S.sth[i];
             }
             __sincosf(th, &sn, &cs);
             npx = x + k.l * cs;
@@ -420,7 +427,7 @@ static __device__ __forceinline__ void run_env_nav4(const LaunchArgs<float>& A, 
     if (A.io.ret && i == 0) A.io.ret[e] = ret_acc;
     if (own) {
         A.s.x[row] = x; A.s.y[row] = y; A.s.th[row] = th;
-        A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.level[row] = lv;
+        A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.gth[row] = gth; A.s.level[row] = lv;
     }
     if (i == 0) {
         A.s.t[e] = t;

@@ -439,19 +439,20 @@ static __device__ __noinline__ QPResult small_resolve_f64(const Team<4> tm, Team
     return qp_solve<double, 4, 4>(tm, D, N, dc);  // the minimiser is left in D.ux / D.uy
 }
 
-// Auto-reset: samples episode ep into S.fx/fy/fth (poses), S.sx/sy (goals), S.slevel (levels)
-// and the resources; returns the resource count.
+// Auto-reset: samples episode ep into S.fx/fy/fth (poses), S.sx/sy/sth (goal positions and
+// headings), S.slevel (levels) and the resources; returns the resource count.
 static __device__ __noinline__ int small_reset(const Team<4> tm, TeamSmem<float, 4>& S,
                                         const LaunchArgs<float> A, int e, int ep, int N) {
     int n_res = 0;
     team_sample<float, 4, 4>(tm, S, A, e, ep, N, n_res);
     const int i = tm.lane;
     if (i < N) {
-        float gx, gy;
+        float gx, gy, gth;
         int lv;
-        robot_goal_level<float>(A, e, ep, i, gx, gy, lv);
+        robot_goal_level<float>(A, e, ep, i, gx, gy, gth, lv);
         S.sx[i] = gx;
         S.sy[i] = gy;
+        S.sth[i] = gth;
         S.slevel[i] = lv;
     }
     tm.sync();
@@ -547,7 +548,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     qc.tol_abs = 2e-7f; qc.tol_rel = 1e-6f; qc.eps_dep = 1e-5f; qc.tol_lam = 1e-6f;
 
     float x = A.s.x[row], y = A.s.y[row], th = A.s.th[row];
-    float gx = A.s.gx[row], gy = A.s.gy[row];
+    float gx = A.s.gx[row], gy = A.s.gy[row], gth = A.s.gth[row];
     int lv = A.s.level[row];
     float sn, cs;
     __sincosf(th, &sn, &cs);
@@ -590,8 +591,12 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         } else {
             float tx = gx, ty = gy;
             if (forage) small_forage_target(S, n_res, px, py, tx, ty);
-            ux = k.k_si * (tx - px);
-            uy = k.k_si * (ty - py);
+            if (!FAST && !forage && k.controller == 1) {
+                pose_nominal<float>(k, x, y, th, gx, gy, gth, ux, uy);
+            } else {
+                ux = k.k_si * (tx - px);
+                uy = k.k_si * (ty - py);
+            }
             cap_fast(ux, uy, k.vmax);
             // Noise words of this robot for step t.  Robots 2m and 2m+1 share the Philox block
             // (pair m, step t); their two lanes compute the blocks of steps t and t+1 at once
@@ -667,10 +672,10 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         if (!forage && k.waypoint && own) {
             const float ex = npx - gx, ey = npy - gy;
             if (ex * ex + ey * ey < k.goal_eps2) {
-                const float2 g = waypoint_goal(A.seed, A.sc.lox, A.sc.loy, A.sc.wx, A.sc.wy, e,
-                                               ep, i, t + 1);
+                const float3 g = waypoint_goal(A.sc, A.seed, e, ep, i, t + 1);
                 gx = g.x;
                 gy = g.y;
+                gth = g.z;
                 flags_l += 256;  // arrivals in bits 8..15
             }
         }
@@ -725,7 +730,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
             n_res = small_reset(tm, S, A, e, ep, N);
             if (own) {
                 x = S.fx[i]; y = S.fy[i]; th = S.fth[i];
-                gx = S.sx[i]; gy = S.sy[i]; lv = S.slevel[i];
+                gx = S.sx[i]; gy = S.sy[i]; gth = S.sth[i]; lv = S.slevel[i];
             }
             tm.sync();
             __sincosf(th, &sn, &cs);
@@ -791,7 +796,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     if (A.io.ret && i == 0) A.io.ret[e] = ret_acc;
     if (own) {
         A.s.x[row] = x; A.s.y[row] = y; A.s.th[row] = th;
-        A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.level[row] = lv;
+        A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.gth[row] = gth; A.s.level[row] = lv;
     }
     if (forage) {
         tm.sync();

@@ -41,8 +41,9 @@ struct StepConsts {
     R gamma, r2, l, inv_l, vmax, half_track, inv_track, dt, kg, half_r, k_si, c_col, rho2;
     R xmin, xmax, ymin, ymax, h_flag;
     R goal_eps2;        // Navigation waypoints: squared arrival radius (waypoint != 0)
+    R pk1, pk2, pk3;    // pose controller gains (controller == 1)
     int scenario, scripted, episode_len, max_iter, n_res_min, n_res_max, r_max, n_max_obs;
-    int max_attempts, resolve_f64, noise_on, waypoint;
+    int max_attempts, resolve_f64, noise_on, waypoint, controller;
     float noise_scale;  // 2 * noise amplitude, binary32 (the noise draw is binary32)
 };
 
@@ -55,6 +56,7 @@ struct SamplerConsts {
 template <typename R>
 struct StateView {
     R *x, *y, *th, *gx, *gy;
+    R* gth;  // goal heading (pose controller)
     int32_t* level;
     int32_t *t, *ep, *n_res;
     R *qx, *qy;
@@ -1126,20 +1128,61 @@ __device__ void team_sample(const Team<G>& tm, TeamSmem<R, NMAX>& S, const Launc
 // reset's goal distribution under the counter (env, episode, goal | robot, steps taken in the
 // episode including this one), so it never repeats the reset's draw (counter word 3 = 0).
 // Out of line: arrivals are rare and the hot loop stays small.
-static __device__ __noinline__ float2 waypoint_goal(uint64_t seed, float lox, float loy, float wx,
-                                                    float wy, int e, int ep, int i, int t_after) {
+static __device__ __noinline__ float3 waypoint_goal(const SamplerConsts sc, uint64_t seed, int e,
+                                                    int ep, int i, int t_after) {
     const Words4 w = draw(seed, e, ep, kGoal, i, (uint32_t)t_after);
-    return make_float2(__fadd_rn(lox, __fmul_rn(unit24(w.w[0]), wx)),
-                       __fadd_rn(loy, __fmul_rn(unit24(w.w[1]), wy)));
+    return make_float3(__fadd_rn(sc.lox, __fmul_rn(unit24(w.w[0]), sc.wx)),
+                       __fadd_rn(sc.loy, __fmul_rn(unit24(w.w[1]), sc.wy)),
+                       __fadd_rn(-sc.pif, __fmul_rn(unit24(w.w[2]), sc.twopif)));
+}
+
+// Unicycle pose controller: posture regulation in polar coordinates (Aicardi, Casalino, Bicchi,
+// Balestrino 1995), standing for the pose controller the paper evaluates (Sec. 4.2, Table 2).
+// In the goal's frame rho is the distance to the goal, gam the angle from the heading to the
+// goal's direction and del that direction's angle; v = k1 rho cos(gam) and
+// omega = k2 gam + k1 (sin(gam) cos(gam) / gam)(gam + k3 del) decrease
+// V = (rho^2 + gam^2 + k3 del^2) / 2.  Returned as the projected point's SI velocity.  In
+// binary32 the headings' sines and cosines use the hardware approximation (absolute error
+// below 4e-7 on (-pi, pi]); gam's go through the accurate library function, since
+// sin(gam) / gam would amplify an absolute error near gam = 0.  The nominal velocity stays
+// within about 1e-6 of the binary64 oracle's.
+__device__ __forceinline__ void sincos_r(float a, float* s, float* c) { __sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sincos(a, s, c); }
+
+template <typename R>
+__device__ __forceinline__ void pose_nominal(const StepConsts<R>& k, R x, R y, R th, R gx, R gy,
+                                             R gth, R& ux, R& uy) {
+    const R pi = (R)CUDART_PI, two_pi = (R)(2.0 * CUDART_PI);
+    R cs, sn, cg, sg;
+    sincos_r(th, &sn, &cs);
+    sincos_r(gth, &sg, &cg);
+    auto wrap = [&](R a) { return a > pi ? a - two_pi : (a <= -pi ? a + two_pi : a); };
+    const R dx = x - gx, dy = y - gy;
+    const R xr = cg * dx + sg * dy, yr = -sg * dx + cg * dy;
+    const R thr = wrap(th - gth);
+    const R rho = hypot(xr, yr);
+    R v = (R)0, w = -k.pk2 * thr;  // on the goal point: turn towards the goal heading
+    if (rho > (R)0) {
+        const R gam = wrap(atan2(yr, xr) + pi - thr);
+        const R del = wrap(gam + thr);
+        R sgm, cgm;
+        sincos(gam, &sgm, &cgm);
+        const R sinc = (gam == (R)0) ? (R)1 : sgm / gam;
+        v = k.pk1 * rho * cgm;
+        w = k.pk2 * gam + k.pk1 * sinc * cgm * (gam + k.pk3 * del);
+    }
+    ux = v * cs - k.l * w * sn;
+    uy = v * sn + k.l * w * cs;
 }
 
 // Goal and level of robot i for episode ep (owner lane).
 template <typename R>
 __device__ __forceinline__ void robot_goal_level(const LaunchArgs<R>& A, int e, int ep, int i,
-                                                 R& gx, R& gy, int& lv) {
+                                                 R& gx, R& gy, R& gth, int& lv) {
     const Words4 w = draw(A.seed, e, ep, kGoal, i, 0u);
     gx = (R)__fadd_rn(A.sc.lox, __fmul_rn(unit24(w.w[0]), A.sc.wx));
     gy = (R)__fadd_rn(A.sc.loy, __fmul_rn(unit24(w.w[1]), A.sc.wy));
+    gth = (R)__fadd_rn(-A.sc.pif, __fmul_rn(unit24(w.w[2]), A.sc.twopif));
     lv = 0;
     if (A.k.scenario == 1) {
         const Words4 v = draw(A.seed, e, ep, kLevel, i, 0u);
@@ -1170,7 +1213,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
         qc.tol_abs = (R)1e-12; qc.tol_rel = (R)1e-12; qc.eps_dep = (R)1e-12; qc.tol_lam = (R)1e-10;
     }
 
-    R x[RPL], y[RPL], th[RPL], gx[RPL], gy[RPL], cs[RPL], sn[RPL];
+    R x[RPL], y[RPL], th[RPL], gx[RPL], gy[RPL], gth[RPL], cs[RPL], sn[RPL];
     int lv[RPL];
 #pragma unroll
     for (int s = 0; s < RPL; ++s) {
@@ -1180,6 +1223,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
         if (i < N) {
             x[s] = A.s.x[off + i]; y[s] = A.s.y[off + i]; th[s] = A.s.th[off + i];
             gx[s] = A.s.gx[off + i]; gy[s] = A.s.gy[off + i]; lv[s] = A.s.level[off + i];
+            gth[s] = A.s.gth[off + i];
             sc_(th[s], &sn[s], &cs[s]);
         }
     }
@@ -1228,8 +1272,12 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                         if (best >= 0) { tx = S.qx[best]; ty = S.qy[best]; }
                         else { tx = px; ty = py; }
                     }
-                    ux = k.k_si * (tx - px);
-                    uy = k.k_si * (ty - py);
+                    if (!forage && k.controller == 1) {
+                        pose_nominal<R>(k, x[s], y[s], th[s], gx[s], gy[s], gth[s], ux, uy);
+                    } else {
+                        ux = k.k_si * (tx - px);
+                        uy = k.k_si * (ty - py);
+                    }
                     cap_norm(ux, uy, k.vmax);
                     if (k.noise_on) {
                         const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)t);
@@ -1361,10 +1409,10 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 if (!forage && k.waypoint) {
                     const R ex = pxi - gx[s], ey = pyi - gy[s];
                     if (ex * ex + ey * ey < k.goal_eps2) {
-                        const float2 g = waypoint_goal(A.seed, A.sc.lox, A.sc.loy, A.sc.wx,
-                                                       A.sc.wy, e, ep, i, t + 1);
+                        const float3 g = waypoint_goal(A.sc, A.seed, e, ep, i, t + 1);
                         gx[s] = (R)g.x;
                         gy[s] = (R)g.y;
+                        gth[s] = (R)g.z;
                         ++arr_l;
                     }
                 }
@@ -1437,7 +1485,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                     y[s] = (R)S.fy[i];
                     th[s] = (R)S.fth[i];
                     sc_(th[s], &sn[s], &cs[s]);
-                    robot_goal_level<R>(A, e, ep, i, gx[s], gy[s], lv[s]);
+                    robot_goal_level<R>(A, e, ep, i, gx[s], gy[s], gth[s], lv[s]);
                 }
             }
             tm.sync();
@@ -1515,6 +1563,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
         if (i < N) {
             A.s.x[off + i] = x[s]; A.s.y[off + i] = y[s]; A.s.th[off + i] = th[s];
             A.s.gx[off + i] = gx[s]; A.s.gy[off + i] = gy[s]; A.s.level[off + i] = lv[s];
+            A.s.gth[off + i] = gth[s];
         }
     }
     if (forage) {
@@ -1547,14 +1596,15 @@ __device__ void reset_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R,
     for (int s = 0; s < RPL; ++s) {
         const int i = tm.lane + s * G;
         if (i < N) {
-            R gx, gy;
+            R gx, gy, gth;
             int lv;
-            robot_goal_level<R>(A, e, ep, i, gx, gy, lv);
+            robot_goal_level<R>(A, e, ep, i, gx, gy, gth, lv);
             A.s.x[off + i] = (R)S.fx[i];
             A.s.y[off + i] = (R)S.fy[i];
             A.s.th[off + i] = (R)S.fth[i];
             A.s.gx[off + i] = gx;
             A.s.gy[off + i] = gy;
+            A.s.gth[off + i] = gth;
             A.s.level[off + i] = lv;
         }
     }

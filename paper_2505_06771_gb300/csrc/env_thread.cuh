@@ -18,14 +18,14 @@ namespace rl {
 // Reset sampler of one env of N <= 4 robots in one thread (binary32, one rounding per
 // operation; the same draws as team_sample).
 struct ThreadPose {
-    float x[4], y[4], th[4], gx[4], gy[4];
+    float x[4], y[4], th[4], gx[4], gy[4], gth[4];
 };
 
 static __device__ __noinline__ ThreadPose thread_sample(const SamplerConsts sc, uint64_t seed,
                                                         int max_att, int e, int ep, int N) {
     ThreadPose P;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) P.x[i] = P.y[i] = P.th[i] = P.gx[i] = P.gy[i] = 0.f;
+    for (int i = 0; i < 4; ++i) P.x[i] = P.y[i] = P.th[i] = P.gx[i] = P.gy[i] = P.gth[i] = 0.f;
     {
         const Words4 w = draw(seed, e, ep, kPos, 0, 0u);
         P.x[0] = __fadd_rn(sc.lox, __fmul_rn(unit24(w.w[0]), sc.wx));
@@ -86,6 +86,7 @@ static __device__ __noinline__ ThreadPose thread_sample(const SamplerConsts sc, 
             const Words4 w = draw(seed, e, ep, kGoal, i, 0u);
             P.gx[i] = __fadd_rn(sc.lox, __fmul_rn(unit24(w.w[0]), sc.wx));
             P.gy[i] = __fadd_rn(sc.loy, __fmul_rn(unit24(w.w[1]), sc.wy));
+            P.gth[i] = __fadd_rn(-sc.pif, __fmul_rn(unit24(w.w[2]), sc.twopif));
         }
     }
     return P;
@@ -120,12 +121,12 @@ __device__ void run_env_thread(const LaunchArgs<float>& A, int e, QPWork<double,
     qc.max_iter = k.max_iter;
     qc.tol_abs = 2e-7f; qc.tol_rel = 1e-6f; qc.eps_dep = 1e-5f; qc.tol_lam = 1e-6f;
 
-    float x[4], y[4], th[4], gx[4], gy[4], cs[4], sn[4];
+    float x[4], y[4], th[4], gx[4], gy[4], gth[4], cs[4], sn[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int row = off + (i < N ? i : 0);
         x[i] = A.s.x[row]; y[i] = A.s.y[row]; th[i] = A.s.th[row];
-        gx[i] = A.s.gx[row]; gy[i] = A.s.gy[row];
+        gx[i] = A.s.gx[row]; gy[i] = A.s.gy[row]; gth[i] = A.s.gth[row];
         __sincosf(th[i], &sn[i], &cs[i]);
     }
     int t = A.s.t[e], ep = A.s.ep[e];
@@ -223,10 +224,10 @@ __device__ void run_env_thread(const LaunchArgs<float>& A, int e, QPWork<double,
                 if (k.waypoint) {
                     const float ex = npx[i] - gx[i], ey = npy[i] - gy[i];
                     if (ex * ex + ey * ey < k.goal_eps2) {
-                        const float2 g = waypoint_goal(A.seed, A.sc.lox, A.sc.loy, A.sc.wx,
-                                                       A.sc.wy, e, ep, i, t + 1);
+                        const float3 g = waypoint_goal(A.sc, A.seed, e, ep, i, t + 1);
                         gx[i] = g.x;
                         gy[i] = g.y;
+                        gth[i] = g.z;
                         ++c_succ;
                     }
                 }
@@ -250,6 +251,7 @@ __device__ void run_env_thread(const LaunchArgs<float>& A, int e, QPWork<double,
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 x[i] = P.x[i]; y[i] = P.y[i]; th[i] = P.th[i]; gx[i] = P.gx[i]; gy[i] = P.gy[i];
+                gth[i] = P.gth[i];
                 __sincosf(th[i], &sn[i], &cs[i]);
             }
         }
@@ -300,7 +302,7 @@ __device__ void run_env_thread(const LaunchArgs<float>& A, int e, QPWork<double,
     for (int i = 0; i < 4; ++i) {
         if (i < N) {
             A.s.x[off + i] = x[i]; A.s.y[off + i] = y[i]; A.s.th[off + i] = th[i];
-            A.s.gx[off + i] = gx[i]; A.s.gy[off + i] = gy[i];
+            A.s.gx[off + i] = gx[i]; A.s.gy[off + i] = gy[i]; A.s.gth[off + i] = gth[i];
         }
     }
     A.s.t[e] = t;

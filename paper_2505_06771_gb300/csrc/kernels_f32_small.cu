@@ -17,6 +17,7 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     const size_t smem = (size_t)tpb * sizeof(TeamSmem<float, 4>);
     const bool fast = is_fast(a);
     int variant = a.variant;
+    if (fast && a.k.controller != 0) variant = 2;  // the pose controller: gather kernel only
     if (fast && variant != 1 && variant != 2) {
         // auto: the gather kernel (lower latency per step) for small batches, the shuffle
         // kernel (fewer instructions per env-step) for large ones; measured on GB300, 4096
@@ -66,7 +67,7 @@ cudaError_t launch_f32_small(const LaunchArgs<float>& a, int lanes, int block_th
         case 1:
             // Navigation, scripted, no traces: one thread per env; otherwise the 4-lane team
             if (reset) return launch_one<float, 4, 4>(a, 64, max_blocks, st, true);
-            if (is_fast(a)) return launch_thread(a, block_threads, max_blocks, st);
+            if (is_fast(a) && a.k.controller == 0) return launch_thread(a, block_threads, max_blocks, st);
             return launch_small_regs(a, 64, max_blocks, st);
         case 2: return launch_one<float, 2, 4>(a, block_threads, max_blocks, st, reset);
         case 4:

@@ -20,10 +20,10 @@
 namespace {
 
 constexpr uint32_t kMagic = 0x31534C52u;  // "RLS1"
-constexpr uint32_t kVersion = 1u;
-constexpr int kSegs = 16;
+constexpr uint32_t kVersion = 2u;
+constexpr int kSegs = 17;
 enum Seg { S_X = 0, S_Y, S_TH, S_GX, S_GY, S_LEVEL, S_T, S_EP, S_NRES, S_QX, S_QY, S_QLEVEL,
-           S_QACTIVE, S_COUNTERS, S_NROB, S_OFF };
+           S_QACTIVE, S_COUNTERS, S_NROB, S_OFF, S_GTH };
 
 struct StateHeader {
     uint32_t magic, version;
@@ -101,6 +101,13 @@ bool valid_cfg(const rl_config& c, std::string& why) {
         why = "goal_eps";
         return false;
     }
+    if ((c.controller != RL_CTRL_POSITION && c.controller != RL_CTRL_POSE) ||
+        (c.controller == RL_CTRL_POSE &&
+         (c.scenario != RL_SCEN_NAVIGATION || !(c.pose_k1 > 0) || !(c.pose_k2 > 0) ||
+          !(c.pose_k3 > 0)))) {
+        why = "controller";
+        return false;
+    }
     return true;
 }
 
@@ -109,7 +116,7 @@ void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
     const rl_config& c = h->cfg;
     auto seg = [&](int s) { return (void*)(h->d_img + h->seg_off[s]); };
     a.s.x = (R*)seg(S_X); a.s.y = (R*)seg(S_Y); a.s.th = (R*)seg(S_TH);
-    a.s.gx = (R*)seg(S_GX); a.s.gy = (R*)seg(S_GY);
+    a.s.gx = (R*)seg(S_GX); a.s.gy = (R*)seg(S_GY); a.s.gth = (R*)seg(S_GTH);
     a.s.level = (int32_t*)seg(S_LEVEL);
     a.s.t = (int32_t*)seg(S_T); a.s.ep = (int32_t*)seg(S_EP); a.s.n_res = (int32_t*)seg(S_NRES);
     a.s.qx = (R*)seg(S_QX); a.s.qy = (R*)seg(S_QY);
@@ -132,6 +139,8 @@ void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
     k.h_flag = (R)c.h_flag;
     k.goal_eps2 = (R)(c.goal_eps * c.goal_eps);
     k.waypoint = (c.scenario == RL_SCEN_NAVIGATION && c.goal_eps > 0.0) ? 1 : 0;
+    k.controller = c.controller;
+    k.pk1 = (R)c.pose_k1; k.pk2 = (R)c.pose_k2; k.pk3 = (R)c.pose_k3;
     k.scenario = c.scenario; k.scripted = c.scripted; k.episode_len = c.episode_len;
     k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * h->n_max + 16;
     k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = h->r_max;
@@ -341,6 +350,11 @@ rl_status rl_config_default(int32_t scenario, rl_config* out) {
     out->near_dmin = 0.18;
     out->near_dmax = 0.20;
     out->h_flag = 1e-3;
+    out->goal_eps = 0.0;
+    out->controller = RL_CTRL_POSITION;
+    out->pose_k1 = 1.0;
+    out->pose_k2 = 2.0;
+    out->pose_k3 = 1.0;
     return RL_OK;
 }
 
@@ -378,7 +392,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     const size_t E = (size_t)n_envs, T = (size_t)h->total, RM = (size_t)h->r_max * E;
     const size_t lens[kSegs] = {T * h->esz, T * h->esz, T * h->esz, T * h->esz, T * h->esz,
                                 T * 4, E * 4, E * 4, E * 4, RM * h->esz, RM * h->esz, RM * 4,
-                                RM * 4, E * rl::kNCount * 4, E * 4, (E + 1) * 4};
+                                RM * 4, E * rl::kNCount * 4, E * 4, (E + 1) * 4, T * h->esz};
     size_t pos = 0;
     for (int s = 0; s < kSegs; ++s) {
         h->seg_off[s] = pos;
@@ -824,7 +838,7 @@ size_t request_bytes(const rl_config& c, const rl_request& r) {
     const size_t es = c.precision == RL_PREC_F64 ? 8 : 4;
     const size_t RM = c.scenario == RL_SCEN_FORAGING ? E * (size_t)c.r_max : 0;
     auto a = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    return 5 * a(rows * es) + a(rows * 4) + 3 * a(E * 4) + 2 * a(RM * es) + 2 * a(RM * 4) +
+    return 6 * a(rows * es) + a(rows * 4) + 3 * a(E * 4) + 2 * a(RM * es) + 2 * a(RM * 4) +
            a(E * rl::kNCount * 4) + a(E * 4) + a((E + 1) * 4) + a(E * 4) + a(E * es) + 4096;
 }
 

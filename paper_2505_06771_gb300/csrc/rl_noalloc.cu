@@ -68,6 +68,7 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     a.s.th = (R*)take(rows * es);
     a.s.gx = (R*)take(rows * es);
     a.s.gy = (R*)take(rows * es);
+    a.s.gth = (R*)take(rows * es);
     a.s.level = (int32_t*)take(rows * 4);
     a.s.t = (int32_t*)take((size_t)E * 4);
     a.s.ep = (int32_t*)take((size_t)E * 4);
@@ -97,6 +98,8 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     k.h_flag = (R)c.h_flag;
     k.goal_eps2 = (R)(c.goal_eps * c.goal_eps);
     k.waypoint = (c.scenario == RL_SCEN_NAVIGATION && c.goal_eps > 0.0) ? 1 : 0;
+    k.controller = c.controller;
+    k.pk1 = (R)c.pose_k1; k.pk2 = (R)c.pose_k2; k.pk3 = (R)c.pose_k3;
     k.scenario = c.scenario; k.scripted = 1; k.episode_len = c.episode_len;
     k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * n_max + 16;
     k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = r_max;
@@ -159,7 +162,7 @@ extern "C" size_t rl_noalloc_state_bytes(const rl_config* c, int32_t n_envs, int
     const size_t E = (size_t)n_envs, rows = E * (size_t)n_robots;
     const size_t es = c->precision == RL_PREC_F64 ? 8 : 4;
     const size_t RM = c->scenario == RL_SCEN_FORAGING ? E * (size_t)c->r_max : 0;
-    return 5 * align256(rows * es) + align256(rows * 4) + 3 * align256(E * 4) +
+    return 6 * align256(rows * es) + align256(rows * 4) + 3 * align256(E * 4) +
            2 * align256(RM * es) + 2 * align256(RM * 4) + align256(E * rl::kNCount * 4) +
            align256(E * 4) + align256((E + 1) * 4);
 }
@@ -181,6 +184,11 @@ extern "C" rl_status rl_rollout_noalloc(const rl_config* cfg, int32_t n_envs, in
         !(c.ymax > c.ymin))
         return RL_ERR_ARG;
     if (!(c.goal_eps >= 0.0) || (c.goal_eps > 0.0 && c.scenario != RL_SCEN_NAVIGATION))
+        return RL_ERR_ARG;
+    if ((c.controller != RL_CTRL_POSITION && c.controller != RL_CTRL_POSE) ||
+        (c.controller == RL_CTRL_POSE &&
+         (c.scenario != RL_SCEN_NAVIGATION || !(c.pose_k1 > 0) || !(c.pose_k2 > 0) ||
+          !(c.pose_k3 > 0))))
         return RL_ERR_ARG;
     if (rl_noalloc_state_bytes(cfg, n_envs, n_robots) > kStaticBytes) return RL_ERR_ARG;
     void* base = nullptr;

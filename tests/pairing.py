@@ -28,7 +28,7 @@ def make_pair(scenario, n_max, precision=32, **kw):
 def to_oracle_state(ocfg, st):
     """oracle.State from a parsed GPU state blob (values widened to double exactly)."""
     s = oracle.State(ocfg, st["n_robots"])
-    for k in ("x", "y", "th", "gx", "gy"):
+    for k in ("x", "y", "th", "gx", "gy", "gth"):
         getattr(s, k)[:] = st[k].astype(np.float64)
     s.level[:] = st["level"]
     s.t[:] = st["t"]

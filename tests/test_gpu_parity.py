@@ -45,7 +45,7 @@ def _alloc(env, T=None):
 
 def _check_reset_state(g, o, st, n_robots, seed):
     s = oracle.reset(o, seed, n_robots)
-    for k in ("x", "y", "th", "gx", "gy"):
+    for k in ("x", "y", "th", "gx", "gy", "gth"):
         assert np.array_equal(st[k].astype(np.float64), getattr(s, k)), k
     assert np.array_equal(st["level"], s.level)
     assert np.array_equal(st["n_res"], s.n_res)
@@ -119,6 +119,7 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
         # goals change only through exact draws (reset, waypoint arrival)
         assert np.array_equal(st2["gx"].astype(np.float64), s.gx), f"goals differ at step {t}"
         assert np.array_equal(st2["gy"].astype(np.float64), s.gy), f"goals differ at step {t}"
+        assert np.array_equal(st2["gth"].astype(np.float64), s.gth), f"goal headings differ at {t}"
         if o["r_max"] > 0:
             assert np.array_equal(st2["qactive"], s.qactive), f"resources differ at step {t}"
         cg, co = st2["counters"], s.counters.reshape(-1, 8)
@@ -219,6 +220,31 @@ def test_waypoint_arrivals_counted_in_rollout(rl):
     assert succ >= changes > 0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case", ["nav4", "nav4_fast_path_off", "nav10", "nav4_f64",
+                                  "nav4_waypoint"])
+def test_teacher_forced_pose_controller(rl, case):
+    """Navigation under the unicycle pose controller (goal heading drawn with the goal): the
+    nominal command, the filtered command and the step against the oracle stepped from the same
+    state, for the 4-robot register kernel, the 10-robot team kernel, binary64 and waypoint
+    mode (goal pose redrawn on arrival).  Without traces the step takes the gather kernel, the
+    one Navigation fast path that implements the pose controller."""
+    N = 10 if case == "nav10" else 4
+    prec = 64 if case == "nav4_f64" else 32
+    kw = dict(controller=1, episode_len=30)
+    if case == "nav4_waypoint":
+        kw.update(goal_eps=0.35, episode_len=10_000)
+    g, o = make_pair(0, N, prec, **kw)
+    E = 96 if N == 10 else 300
+    err, _ = _teacher_forced(rl, g, o, [N] * E, 29, 40, traces=(case != "nav4_fast_path_off"))
+    print(f"\npose controller {case}: max errors {err}")
+    # the pose law is a chain of trigonometric functions: in binary32 its nominal velocity is
+    # held to the control tolerance (1e-5), not the 1e-6 of the position law
+    tol = 1e-8 if prec == 64 else 1.0
+    assert err["u_nom"] < U_TOL * tol and err["u_star"] < U_TOL * tol
+    assert err["pose"] < 1e-6 * tol and err["th"] < 1e-5 * tol
+    assert err["rew"] < 1e-5 * tol and err["obs"] < 1e-5 * tol
 
 
 def test_teacher_forced_binary64(rl):

@@ -36,12 +36,14 @@ def test_defaults_agree_with_oracle(rl):
 def test_state_blob_parser_layout():
     import numpy as np
     import paper_2505_06771_gb300 as m
-    # header + image of 16 segments for E=2 envs, 5 robots, binary32, no resources
+    # header + image of 17 segments for E=2 envs, 5 robots, binary32, no resources
     E, T = 2, 5
-    lens = [T * 4] * 5 + [T * 4, E * 4, E * 4, E * 4, 0, 0, 0, 0, E * 32, E * 4, (E + 1) * 4]
+    lens = [T * 4] * 5 + [T * 4, E * 4, E * 4, E * 4, 0, 0, 0, 0, E * 32, E * 4, (E + 1) * 4,
+                          T * 4]
     img = b"".join(bytes([i + 1]) * n + b"\0" * (((n + 255) & ~255) - n) for i, n in enumerate(lens))
-    hdr = np.array([0x31534C52, 1, 32, 0, E, T, 0, 3], np.int32).tobytes()
+    hdr = np.array([0x31534C52, 2, 32, 0, E, T, 0, 3], np.int32).tobytes()
     hdr += np.array([7, len(img)], np.uint64).tobytes() + b"\0" * 16
     st = m.parse_state(hdr + img)
     assert st["n_envs"] == 2 and st["seed"] == 7
     assert st["x"].view(np.uint8)[0] == 1 and st["off"].view(np.uint8)[0] == 16
+    assert st["gth"].view(np.uint8)[0] == 17 and len(st["gth"]) == T
