@@ -55,6 +55,9 @@ WORKLOADS = {
                      context={"paper_table2_ms_per_10k_steps": 9.18,
                               "paper_hardware": "JAX on an Apple M4 Pro CPU (position "
                                                 "controller); another machine: context only"}),
+    "discovery": dict(desc="discovery: 4096 envs x 4 robots (2 sensing, 2 tagging) x 1000 steps, "
+                           "U{2..6} landmarks, fp32",
+                      scenario=2, E=4096, N=4, T=1000, precision=32, near=0.0, n_max=4),
     "waypoint_pose": dict(desc="random waypoint navigation under the unicycle pose controller: 1 "
                                "env x 4 robots x 10000 steps, a new goal pose on arrival within "
                                "0.05 m, fp32 (Table 2's pose-controller row)",
@@ -73,7 +76,8 @@ KERNELS = {"nav": "rl::env_kernel_small<1> (4-robot shuffle team kernel)",
            "uneven": "rl::env_kernel_multi (one persistent launch over all size classes)",
            "largen": "rl::env_kernel<float, 32, 20> (20-robot class, explicit-inverse QP)",
            "tiny": "rl::env_kernel<double, 4, 4> (binary64 team kernel)",
-           "waypoint_pose": "rl::env_kernel_small<2> (4-robot gather team kernel, pose controller)"}
+           "waypoint_pose": "rl::env_kernel_small<2> (4-robot gather team kernel, pose controller)",
+           "discovery": "rl::env_kernel_small<0> (4-robot general team kernel)"}
 
 
 def _args():

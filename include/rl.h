@@ -54,7 +54,7 @@ typedef enum {
     RL_ERR_BUDGET = 6    /* a request can never fit the memory budget */
 } rl_status;
 
-typedef enum { RL_SCEN_NAVIGATION = 0, RL_SCEN_FORAGING = 1 } rl_scenario;
+typedef enum { RL_SCEN_NAVIGATION = 0, RL_SCEN_FORAGING = 1, RL_SCEN_DISCOVERY = 2 } rl_scenario;
 typedef enum { RL_CTRL_POSITION = 0, RL_CTRL_POSE = 1 } rl_controller;
 
 typedef enum { RL_PREC_F32 = 32, RL_PREC_F64 = 64 } rl_precision;
@@ -117,6 +117,8 @@ typedef struct {
                                Navigation, Sec. 4.2); 0 (default) keeps goals for the episode */
     double pose_k1, pose_k2, pose_k3;  /* pose controller gains: approach, heading, final
                                           orientation weight (1, 2, 1), all > 0 */
+    double sense_radius, tag_radius;   /* Discovery capabilities (App. B: 0.45 m, 0.25 m) */
+    double sense_reward, tag_reward, step_penalty;  /* Discovery rewards (App. B: 1, 5, 0.05) */
 } rl_config;
 
 /* Optional outputs of one step (any pointer may be NULL). */

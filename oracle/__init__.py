@@ -29,7 +29,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-NAV, FORAGE = 0, 1
+NAV, FORAGE, DISCOVERY = 0, 1, 2
 NCOUNT = 8
 CNT_COLLISIONS, CNT_OOB, CNT_SUCCESS, CNT_QP_ACTIVE = 0, 1, 2, 3
 CNT_QP_FLAGGED, CNT_QP_INFEASIBLE, CNT_EPISODES, CNT_QP_ITERS = 4, 5, 6, 7
@@ -58,7 +58,8 @@ class Cfg(ctypes.Structure):
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
                  "near_frac", "near_dmin", "near_dmax", "goal_eps", "pose_k1", "pose_k2",
-                 "pose_k3")]
+                 "pose_k3", "sense_radius", "tag_radius", "sense_reward", "tag_reward",
+                 "step_penalty")]
 
 
 _P = ctypes.POINTER
@@ -111,9 +112,11 @@ def default_cfg(scenario: int = NAV, n_max: int = 4, **overrides) -> dict:
     U(-0.05, 0.05), collision penalty 1 (Navigation) / 0 (Foraging, App. B), foraging radius
     0.25 m, initial poses >= 0.3 m apart and >= 0.2 m from the walls."""
     c = dict(scenario=scenario, scripted=1, episode_len=100, n_res_min=2, n_res_max=6,
-             max_attempts=4096, n_max=n_max, r_max=6 if scenario == FORAGE else 0,
+             max_attempts=4096, n_max=n_max, r_max=0 if scenario == NAV else 6,
              gamma=100.0, r=0.17, l=0.05, vmax=0.2, wmax=3.6, dt=0.033, kappa=0.4, k_si=1.0,
              noise_amp=0.05, c_col=1.0 if scenario == NAV else 0.0, forage_radius=0.25,
+             sense_radius=0.45, tag_radius=0.25, sense_reward=1.0, tag_reward=5.0,
+             step_penalty=0.05,
              xmin=-1.6, xmax=1.6, ymin=-1.0, ymax=1.0, init_margin=0.2, min_sep=0.3,
              near_frac=0.0, near_dmin=0.18, near_dmax=0.20, goal_eps=0.0, controller=0,
              pose_k1=1.0, pose_k2=2.0, pose_k3=1.0)

@@ -91,6 +91,7 @@ static int32_t below(uint32_t w, uint32_t k) { return (int32_t)(((uint64_t)w * k
 
 int orc_obs_dim(const orc_cfg* c) {
     if (c->scenario == ORC_FORAGE) return 4 + 4 * (c->n_max - 1) + 4 * c->r_max;
+    if (c->scenario == ORC_DISCOVERY) return 5 + 5 * (c->n_max - 1) + 4 * c->r_max;
     return 5 + 3 * (c->n_max - 1);
 }
 
@@ -220,6 +221,21 @@ static void sample_env(const orc_cfg* c, uint64_t seed, int e, int ep, int n, en
         s->level[i] = 0;
     }
     s->n_res = 0;
+    if (c->scenario == ORC_DISCOVERY) {
+        /* Discovery (App. B): the first ceil(n/2) robots sense (role 1), the others tag (role
+           2); K landmarks uniform in the arena region, none sensed (qlevel 0) or tagged
+           (qactive 1 = still to tag) */
+        for (int i = 0; i < n; ++i) s->level[i] = (i < (n + 1) / 2) ? 1 : 2;
+        draw(seed, e, ep, P_NRES, 0, 0, w);
+        s->n_res = c->n_res_min + below(w[0], (uint32_t)(c->n_res_max - c->n_res_min + 1));
+        for (int k = 0; k < s->n_res; ++k) {
+            draw(seed, e, ep, P_RES, k, 0, w);
+            s->qx[k] = (double)(lox + u01(w[0]) * wx);
+            s->qy[k] = (double)(loy + u01(w[1]) * wy);
+            s->qlevel[k] = 0;
+            s->qactive[k] = 1;
+        }
+    }
     if (c->scenario == ORC_FORAGE) {
         for (int i = 0; i < n; ++i) {
             draw(seed, e, ep, P_LEVEL, i, 0, w);
@@ -503,7 +519,39 @@ static void write_obs(const orc_cfg* c, const env_t* s, double* obs) {
         double* o = obs + (size_t)i * od;
         for (int k = 0; k < od; ++k) o[k] = 0.0;
         int base;
-        if (c->scenario == ORC_FORAGE) {
+        if (c->scenario == ORC_DISCOVERY) {
+            /* own pose and capability [sensing radius, tagging radius]; the others' relative
+               poses and capabilities; landmarks: relative position, sensed, tagged once sensed,
+               else the relative position of a point outside the arena and zeros (App. B) */
+            const double xo = c->xmax + (c->xmax - c->xmin), yo = c->ymax + (c->ymax - c->ymin);
+            o[0] = s->x[i]; o[1] = s->y[i]; o[2] = s->th[i];
+            o[3] = s->level[i] == 1 ? c->sense_radius : 0.0;
+            o[4] = s->level[i] == 2 ? c->tag_radius : 0.0;
+            int slot = 0;
+            for (int j = 0; j < s->n; ++j) {
+                if (j == i) continue;
+                double* q = o + 5 + 5 * slot;
+                q[0] = s->x[j] - s->x[i];
+                q[1] = s->y[j] - s->y[i];
+                q[2] = wrap_angle(s->th[j] - s->th[i]);
+                q[3] = s->level[j] == 1 ? c->sense_radius : 0.0;
+                q[4] = s->level[j] == 2 ? c->tag_radius : 0.0;
+                ++slot;
+            }
+            base = 5 + 5 * (c->n_max - 1);
+            for (int k = 0; k < s->n_res; ++k) {
+                double* q = o + base + 4 * k;
+                if (s->qlevel[k]) {
+                    q[0] = s->qx[k] - s->x[i];
+                    q[1] = s->qy[k] - s->y[i];
+                    q[2] = 1.0;
+                    q[3] = s->qactive[k] ? 0.0 : 1.0;
+                } else {
+                    q[0] = xo - s->x[i];
+                    q[1] = yo - s->y[i];
+                }
+            }
+        } else if (c->scenario == ORC_FORAGE) {
             o[0] = s->x[i]; o[1] = s->y[i]; o[2] = s->th[i]; o[3] = (double)s->level[i];
             base = 4;
             int slot = 0;
@@ -571,6 +619,22 @@ static void env_step(const orc_cfg* c, uint64_t seed, int e, env_t* s, const dou
             uy = act[2 * i + 1];
         } else {
             double tx = s->gx[i], ty = s->gy[i];
+            if (c->scenario == ORC_DISCOVERY) {
+                /* sensing robots: the nearest landmark not yet sensed; tagging robots: the
+                   nearest sensed one not yet tagged (ties: lowest index); none: hold */
+                int best = -1;
+                double bd = 0.0;
+                for (int k = 0; k < s->n_res; ++k) {
+                    const int want = (s->level[i] == 1) ? !s->qlevel[k]
+                                                        : (s->qlevel[k] && s->qactive[k]);
+                    if (!want) continue;
+                    double dx = s->qx[k] - px[i], dy = s->qy[k] - py[i];
+                    double d2 = dx * dx + dy * dy;
+                    if (best < 0 || d2 < bd) { best = k; bd = d2; }
+                }
+                if (best >= 0) { tx = s->qx[best]; ty = s->qy[best]; }
+                else { tx = px[i]; ty = py[i]; }
+            }
             if (c->scenario == ORC_FORAGE) {
                 /* nearest active resource (ties: lowest index); none: hold position */
                 int best = -1;
@@ -689,6 +753,34 @@ static void env_step(const orc_cfg* c, uint64_t seed, int e, env_t* s, const dou
             }
         }
         all_foraged = (s->n_res > 0 && remaining == 0);
+    } else if (c->scenario == ORC_DISCOVERY) {
+        /* a landmark within the sensing radius of a sensing robot becomes sensed; a sensed
+           landmark within the tagging radius of a tagging robot becomes tagged (in the same
+           step too); rewards per landmark sensed and tagged, a penalty for every step that
+           ends with a landmark still to tag (App. B); each tag counts as a success */
+        const double rs2 = c->sense_radius * c->sense_radius, rt2 = c->tag_radius * c->tag_radius;
+        int remaining = 0;
+        for (int k = 0; k < s->n_res; ++k) {
+            if (!s->qlevel[k]) {
+                for (int i = 0; i < N; ++i) {
+                    double dx = px[i] - s->qx[k], dy = py[i] - s->qy[k];
+                    if (s->level[i] == 1 && dx * dx + dy * dy < rs2) { s->qlevel[k] = 1; break; }
+                }
+                if (s->qlevel[k]) rew += c->sense_reward;
+            }
+            if (s->qlevel[k] && s->qactive[k]) {
+                for (int i = 0; i < N; ++i) {
+                    double dx = px[i] - s->qx[k], dy = py[i] - s->qy[k];
+                    if (s->level[i] == 2 && dx * dx + dy * dy < rt2) { s->qactive[k] = 0; break; }
+                }
+                if (!s->qactive[k]) {
+                    rew += c->tag_reward;
+                    cnt[ORC_CNT_SUCCESS] += 1;
+                }
+            }
+            remaining += s->qactive[k];
+        }
+        if (remaining > 0) rew -= c->step_penalty;
     } else {
         for (int i = 0; i < N; ++i) {
             double d_new = hypot(px[i] - s->gx[i], py[i] - s->gy[i]);
@@ -743,8 +835,10 @@ static void env_step(const orc_cfg* c, uint64_t seed, int e, env_t* s, const dou
 static int check_cfg(const orc_cfg* c, int E, const int32_t* n_robots) {
     if (E < 0 || c->n_max < 1 || c->n_max > ORC_NMAX || c->r_max < 0 || c->r_max > ORC_RMAX)
         return 1;
-    if (c->scenario == ORC_FORAGE && (c->n_res_min < 0 || c->n_res_max > c->r_max ||
-                                      c->n_res_min > c->n_res_max))
+    if (c->scenario != ORC_NAV && c->scenario != ORC_FORAGE && c->scenario != ORC_DISCOVERY)
+        return 1;
+    if (c->scenario != ORC_NAV && (c->n_res_min < 0 || c->n_res_max > c->r_max ||
+                                   c->n_res_min > c->n_res_max))
         return 1;
     if (!(c->goal_eps >= 0.0) || (c->goal_eps > 0.0 && c->scenario != ORC_NAV)) return 1;
     if (c->controller != ORC_CTRL_POSITION && c->controller != ORC_CTRL_POSE) return 1;

@@ -20,7 +20,7 @@
 #define ORC_RMAX 16   /* foraging resources per environment */
 #define ORC_NCOUNT 8  /* int32 counters per environment */
 
-enum { ORC_NAV = 0, ORC_FORAGE = 1 };
+enum { ORC_NAV = 0, ORC_FORAGE = 1, ORC_DISCOVERY = 2 };
 enum { ORC_CTRL_POSITION = 0, ORC_CTRL_POSE = 1 };
 enum { ORC_CNT_COLLISIONS = 0, ORC_CNT_OOB = 1, ORC_CNT_SUCCESS = 2, ORC_CNT_QP_ACTIVE = 3,
        ORC_CNT_QP_FLAGGED = 4, ORC_CNT_QP_INFEASIBLE = 5, ORC_CNT_EPISODES = 6,
@@ -41,6 +41,8 @@ typedef struct {
                               Navigation, Sec. 4.2); 0 keeps the goals for the episode */
     double pose_k1, pose_k2, pose_k3;  /* pose controller gains (approach, heading, final
                                           orientation weight), all > 0 */
+    double sense_radius, tag_radius;   /* Discovery: capability radii (App. B: 0.45, 0.25) */
+    double sense_reward, tag_reward, step_penalty;  /* Discovery rewards (App. B: 1, 5, 0.05) */
 } orc_cfg;
 
 /* Batched structure-of-arrays state.  Robots of env e occupy [off_e, off_e + n_e). */

@@ -20,9 +20,9 @@ from .build import LIB as LIB_PATH
 from .build import build
 
 __all__ = ["build", "lib", "config_default", "Env", "Server", "RLError", "NAVIGATION",
-           "FORAGING", "COUNTERS", "exported_symbols", "rollout_noalloc", "noalloc_state_bytes"]
+           "FORAGING", "DISCOVERY", "COUNTERS", "exported_symbols", "rollout_noalloc", "noalloc_state_bytes"]
 
-NAVIGATION, FORAGING = 0, 1
+NAVIGATION, FORAGING, DISCOVERY = 0, 1, 2
 COUNTERS = ("collisions", "oob", "success", "qp_active", "qp_flagged", "qp_infeasible",
             "episodes", "qp_iters")
 _STATUS = {0: "RL_OK", 1: "RL_ERR_ARG", 2: "RL_ERR_CUDA", 3: "RL_ERR_OOM", 4: "RL_ERR_STATE",
@@ -46,7 +46,8 @@ class RLConfig(ctypes.Structure):
                 ("gamma", "r", "l", "vmax", "wmax", "dt", "kappa", "k_si", "noise_amp", "c_col",
                  "forage_radius", "xmin", "xmax", "ymin", "ymax", "init_margin", "min_sep",
                  "near_frac", "near_dmin", "near_dmax", "h_flag", "goal_eps", "pose_k1",
-                 "pose_k2", "pose_k3")]
+                 "pose_k2", "pose_k3", "sense_radius", "tag_radius", "sense_reward",
+                 "tag_reward", "step_penalty")]
 
 
 class RLRequest(ctypes.Structure):
@@ -315,8 +316,9 @@ def rollout_noalloc(cfg: dict, n_envs: int, n_robots: int, seed: int, T: int, ob
     dt = torch.float64 if cfg["precision"] == 64 else torch.float32
     rows = n_envs * n_robots
     n_max = cfg["n_max"] if cfg["n_max"] > 0 else n_robots
-    od = (4 + 4 * (n_max - 1) + 4 * cfg["r_max"]) if cfg["scenario"] == FORAGING \
-        else 5 + 3 * (n_max - 1)
+    od = {FORAGING: 4 + 4 * (n_max - 1) + 4 * cfg["r_max"],
+          DISCOVERY: 5 + 5 * (n_max - 1) + 4 * cfg["r_max"]}.get(cfg["scenario"],
+                                                                 5 + 3 * (n_max - 1))
     s = stream if stream is not None else torch.cuda.current_stream()
     st = L.rl_rollout_noalloc(ctypes.byref(_to_struct(cfg)), n_envs, n_robots, seed, T,
                               _dptr(obs, dt, T * rows * od, "obs"),

@@ -522,6 +522,47 @@ static __device__ __noinline__ void small_forage_obs(const TeamSmem<float, 4>& S
     }
 }
 
+// Discovery observation of robot i: own pose and capability, the others' relative poses and
+// capabilities, the landmarks (relative position, sensed, tagged; a stand-in point outside the
+// arena while unsensed).
+static __device__ __noinline__ void small_disc_obs(const TeamSmem<float, 4>& S, const StepConsts<float> k,
+                                            float* o, int i, int N, int n_res, float x, float y,
+                                            float th, int lv, const float (&X)[4],
+                                            const float (&Y)[4], const float (&TH)[4],
+                                            const int (&LV)[4]) {
+    o[0] = x; o[1] = y; o[2] = th;
+    o[3] = lv == 1 ? k.sense_r : 0.f;
+    o[4] = lv == 2 ? k.tag_r : 0.f;
+    int c = 5;
+    for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const int lj = pick4(LV, j);
+        o[c] = pick4(X, j) - x;
+        o[c + 1] = pick4(Y, j) - y;
+        o[c + 2] = wrap_pi_f(pick4(TH, j) - th);
+        o[c + 3] = lj == 1 ? k.sense_r : 0.f;
+        o[c + 4] = lj == 2 ? k.tag_r : 0.f;
+        c += 5;
+    }
+    const int rbase = 5 + 5 * (k.n_max_obs - 1);
+    for (; c < rbase; ++c) o[c] = 0.f;
+    for (int r = 0; r < k.r_max; ++r) {
+        if (r < n_res && S.qlevel[r]) {
+            o[c] = S.qx[r] - x;
+            o[c + 1] = S.qy[r] - y;
+            o[c + 2] = 1.f;
+            o[c + 3] = S.qactive[r] ? 0.f : 1.f;
+        } else if (r < n_res) {
+            o[c] = k.xo - x;
+            o[c + 1] = k.yo - y;
+            o[c + 2] = o[c + 3] = 0.f;
+        } else {
+            o[c] = o[c + 1] = o[c + 2] = o[c + 3] = 0.f;
+        }
+        c += 4;
+    }
+}
+
 // One env of at most 4 robots for T steps (team of 4 lanes).  FAST: the Navigation scenario with
 // scripted nominal control and no traces, every such branch folded away at compile time.
 template <bool FAST>
@@ -531,6 +572,8 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     const int off = A.s.off[e];
     const int N = A.s.nrob[e];
     const bool forage = !FAST && (k.scenario == 1);
+    const bool disc = !FAST && (k.scenario == 2);
+    const bool resv = forage || disc;  // per-env resources / landmarks
     const float* actions = FAST ? nullptr : A.io.actions;
     float* tr_unom = FAST ? nullptr : A.io.u_nom;
     float* tr_ustar = FAST ? nullptr : A.io.u_star;
@@ -554,7 +597,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     __sincosf(th, &sn, &cs);
     int t = A.s.t[e], ep = A.s.ep[e];
     int n_res = 0;
-    if (forage) {
+    if (resv) {
         n_res = A.s.n_res[e];
         for (int r = i; r < k.r_max; r += 4) {
             S.qx[r] = A.s.qx[e * k.r_max + r];
@@ -591,7 +634,12 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         } else {
             float tx = gx, ty = gy;
             if (forage) small_forage_target(S, n_res, px, py, tx, ty);
-            if (!FAST && !forage && k.controller == 1) {
+            if (disc && !discovery_target<float>(S.qx, S.qy, S.qlevel, S.qactive, n_res, lv, px, py,
+                                                 tx, ty)) {
+                tx = px;
+                ty = py;
+            }
+            if (!FAST && !resv && k.controller == 1) {
                 pose_nominal<float>(k, x, y, th, gx, gy, gth, ux, uy);
             } else {
                 ux = k.k_si * (tx - px);
@@ -668,8 +716,8 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         }
         flags_l += (own && (npx < k.xmin || npx > k.xmax || npy < k.ymin || npy > k.ymax)) ? 65536 : 0;
         // flags_l: collisions in bits 0..7, waypoint arrivals in 8..15, out-of-arena from 16
-        float rew_l = (!forage && own) ? dold - fast_norm(npx - gx, npy - gy) : 0.f;
-        if (!forage && k.waypoint && own) {
+        float rew_l = (!resv && own) ? dold - fast_norm(npx - gx, npy - gy) : 0.f;
+        if (!resv && k.waypoint && own) {
             const float ex = npx - gx, ey = npy - gy;
             if (ex * ex + ey * ey < k.goal_eps2) {
                 const float3 g = waypoint_goal(A.sc, A.seed, e, ep, i, t + 1);
@@ -706,6 +754,25 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
             }
             all_foraged = (n_res > 0 && remaining == 0);
         }
+        if (disc) {
+            // Discovery: sensing robots sense landmarks within their radius, tagging robots tag
+            // sensed ones within theirs (in the same step too); a penalty while one is left
+            int remaining = 0;
+            for (int r = 0; r < n_res; ++r) {
+                const float dx = npx - S.qx[r], dy = npy - S.qy[r];
+                const float d2 = dx * dx + dy * dy;
+                const bool hs = tm.any(own && lv == 1 && d2 < k.sense_r2);
+                const bool ht = tm.any(own && lv == 2 && d2 < k.tag_r2);
+                int sensed = S.qlevel[r], tagged = S.qactive[r] ? 0 : 1;
+                if (!sensed && hs) { sensed = 1; rew += k.sense_rew; }
+                if (sensed && !tagged && ht) { tagged = 1; rew += k.tag_rew; ++succ; }
+                remaining += tagged ? 0 : 1;
+                tm.sync();
+                if (i == 0) { S.qlevel[r] = sensed; S.qactive[r] = tagged ? 0 : 1; }
+                tm.sync();
+            }
+            if (remaining > 0) rew -= k.step_pen;
+        }
         rew -= k.c_col * (float)col;
         c_col += col;
         c_oob += oob;
@@ -739,7 +806,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         if (A.io.obs) {
             const int od = A.io.obs_dim;
             float* o = A.io.obs + (long long)step * A.io.obs_step + (long long)row * od;
-            if (!forage) {
+            if (!resv) {
                 // others in index order: slot s holds robot s + (s >= i)
                 float rel[9];
 #pragma unroll
@@ -784,7 +851,8 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
                     TH[r] = __shfl_sync(tm.mask, th, r, 4);
                     LV[r] = __shfl_sync(tm.mask, lv, r, 4);
                 }
-                if (own) small_forage_obs(S, k, o, i, N, n_res, x, y, th, lv, X, Y, TH, LV);
+                if (own && disc) small_disc_obs(S, k, o, i, N, n_res, x, y, th, lv, X, Y, TH, LV);
+                else if (own) small_forage_obs(S, k, o, i, N, n_res, x, y, th, lv, X, Y, TH, LV);
             }
         }
         if (i == 0) {
@@ -798,7 +866,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         A.s.x[row] = x; A.s.y[row] = y; A.s.th[row] = th;
         A.s.gx[row] = gx; A.s.gy[row] = gy; A.s.gth[row] = gth; A.s.level[row] = lv;
     }
-    if (forage) {
+    if (resv) {
         tm.sync();
         for (int r = i; r < k.r_max; r += 4) {
             A.s.qx[e * k.r_max + r] = S.qx[r];
@@ -810,7 +878,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
     if (i == 0) {
         A.s.t[e] = t;
         A.s.ep[e] = ep;
-        if (forage) A.s.n_res[e] = n_res;
+        if (resv) A.s.n_res[e] = n_res;
         int32_t* cn = A.s.counters + e * kNCount;
         cn[0] += c_col; cn[1] += c_oob; cn[2] += c_succ; cn[3] += c_act;
         cn[4] += c_flag; cn[5] += c_inf; cn[6] += c_ep; cn[7] += c_it;

@@ -42,6 +42,8 @@ struct StepConsts {
     R xmin, xmax, ymin, ymax, h_flag;
     R goal_eps2;        // Navigation waypoints: squared arrival radius (waypoint != 0)
     R pk1, pk2, pk3;    // pose controller gains (controller == 1)
+    R sense_r2, tag_r2, sense_rew, tag_rew, step_pen;  // Discovery (scenario 2)
+    R sense_r, tag_r, xo, yo;  // capability radii and the unsensed landmarks' stand-in point
     int scenario, scripted, episode_len, max_iter, n_res_min, n_res_max, r_max, n_max_obs;
     int max_attempts, resolve_f64, noise_on, waypoint, controller;
     float noise_scale;  // 2 * noise amplitude, binary32 (the noise draw is binary32)
@@ -1103,7 +1105,8 @@ __device__ void team_sample(const Team<G>& tm, TeamSmem<R, NMAX>& S, const Launc
         tm.sync();
     }
     n_res = 0;
-    if (A.k.scenario == 1) {
+    if (A.k.scenario != 0) {
+        // Foraging resources (level U{1,2,3}) or Discovery landmarks (none sensed: level 0)
         const Words4 w = draw(seed, e, ep, kNRes, 0, 0u);
         n_res = A.k.n_res_min + below(w.w[0], (uint32_t)(A.k.n_res_max - A.k.n_res_min + 1));
         for (int r = tm.lane; r < A.k.r_max; r += G) {
@@ -1111,7 +1114,7 @@ __device__ void team_sample(const Team<G>& tm, TeamSmem<R, NMAX>& S, const Launc
                 const Words4 v = draw(seed, e, ep, kRes, r, 0u);
                 S.qx[r] = (R)__fadd_rn(sc.lox, __fmul_rn(unit24(v.w[0]), sc.wx));
                 S.qy[r] = (R)__fadd_rn(sc.loy, __fmul_rn(unit24(v.w[1]), sc.wy));
-                S.qlevel[r] = 1 + below(v.w[2], 3u);
+                S.qlevel[r] = (A.k.scenario == 1) ? 1 + below(v.w[2], 3u) : 0;
                 S.qactive[r] = 1;
             } else {
                 S.qx[r] = (R)0;
@@ -1188,6 +1191,30 @@ __device__ __forceinline__ void robot_goal_level(const LaunchArgs<R>& A, int e, 
         const Words4 v = draw(A.seed, e, ep, kLevel, i, 0u);
         lv = 1 + below(v.w[0], 3u);
     }
+    // Discovery roles: the first ceil(N/2) robots sense (1), the others tag (2)
+    if (A.k.scenario == 2) lv = (i < (A.s.nrob[e] + 1) / 2) ? 1 : 2;
+}
+
+// Scripted target of a Discovery robot: a sensing robot (role 1) heads for the nearest landmark
+// not yet sensed, a tagging robot for the nearest sensed one not yet tagged (ties: lowest index);
+// false when there is none (the robot holds its position).
+template <typename R>
+__device__ __forceinline__ bool discovery_target(const R* qx, const R* qy, const int* qlevel,
+                                                 const int* qactive, int n_res, int role, R px,
+                                                 R py, R& tx, R& ty) {
+    int best = -1;
+    R bd = (R)0;
+    for (int r = 0; r < n_res; ++r) {
+        const bool want = (role == 1) ? (qlevel[r] == 0) : (qlevel[r] != 0 && qactive[r] != 0);
+        if (!want) continue;
+        const R dx = qx[r] - px, dy = qy[r] - py;
+        const R d2 = dx * dx + dy * dy;
+        if (best < 0 || d2 < bd) { best = r; bd = d2; }
+    }
+    if (best < 0) return false;
+    tx = qx[best];
+    ty = qy[best];
+    return true;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1200,6 +1227,8 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
     const int off = A.s.off[e];
     const int N = A.s.nrob[e];
     const bool forage = (k.scenario == 1);
+    const bool disc = (k.scenario == 2);
+    const bool resv = forage || disc;  // per-env resources / landmarks
     QPWork<R, NMAX>& W = WorkSel<R, NMAX>::get(S.qp);
 
     QPConsts<R> qc;
@@ -1229,7 +1258,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
     }
     int t = A.s.t[e], ep = A.s.ep[e];
     int n_res = 0;
-    if (forage) {
+    if (resv) {
         n_res = A.s.n_res[e];
         for (int r = tm.lane; r < k.r_max; r += G) {
             S.qx[r] = A.s.qx[e * k.r_max + r];
@@ -1272,7 +1301,12 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                         if (best >= 0) { tx = S.qx[best]; ty = S.qy[best]; }
                         else { tx = px; ty = py; }
                     }
-                    if (!forage && k.controller == 1) {
+                    if (disc && !discovery_target<R>(S.qx, S.qy, S.qlevel, S.qactive, n_res,
+                                                     lv[s], px, py, tx, ty)) {
+                        tx = px;
+                        ty = py;
+                    }
+                    if (!resv && k.controller == 1) {
                         pose_nominal<R>(k, x[s], y[s], th[s], gx[s], gy[s], gth[s], ux, uy);
                     } else {
                         ux = k.k_si * (tx - px);
@@ -1290,7 +1324,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 cap_norm(ux, uy, k.vmax);
                 u0x[s] = ux;
                 u0y[s] = uy;
-                if (!forage) dold[s] = hyp(px - gx[s], py - gy[s]);
+                if (!resv) dold[s] = hyp(px - gx[s], py - gy[s]);
                 W.px[i] = px; W.py[i] = py;
                 W.u0x[i] = ux; W.u0y[i] = uy;
                 W.ux[i] = ux; W.uy[i] = uy;
@@ -1405,8 +1439,8 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                     if (dx * dx + dy * dy < k.r2) ++col_l;
                 }
                 if (pxi < k.xmin || pxi > k.xmax || pyi < k.ymin || pyi > k.ymax) ++oob_l;
-                if (!forage) rew_l -= hyp(pxi - gx[s], pyi - gy[s]) - dold[s];
-                if (!forage && k.waypoint) {
+                if (!resv) rew_l -= hyp(pxi - gx[s], pyi - gy[s]) - dold[s];
+                if (!resv && k.waypoint) {
                     const R ex = pxi - gx[s], ey = pyi - gy[s];
                     if (ex * ex + ey * ey < k.goal_eps2) {
                         const float3 g = waypoint_goal(A.sc, A.seed, e, ep, i, t + 1);
@@ -1450,6 +1484,34 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 }
             }
             all_foraged = (n_res > 0 && remaining == 0);
+        }
+        if (disc) {
+            // Discovery: sensing robots sense landmarks within their radius, tagging robots tag
+            // sensed ones within theirs (in the same step too); a penalty while one is left
+            int remaining = 0;
+            for (int r = 0; r < n_res; ++r) {
+                int sensed = S.qlevel[r], tagged = S.qactive[r] ? 0 : 1;
+                int hs = 0, ht = 0;
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        const R dx = W.px[i] - S.qx[r], dy = W.py[i] - S.qy[r];
+                        const R d2 = dx * dx + dy * dy;
+                        hs |= (lv[s] == 1 && d2 < k.sense_r2) ? 1 : 0;
+                        ht |= (lv[s] == 2 && d2 < k.tag_r2) ? 1 : 0;
+                    }
+                }
+                hs = tm.any(hs != 0) ? 1 : 0;
+                ht = tm.any(ht != 0) ? 1 : 0;
+                if (!sensed && hs) { sensed = 1; rew += k.sense_rew; }
+                if (sensed && !tagged && ht) { tagged = 1; rew += k.tag_rew; ++succ; }
+                remaining += tagged ? 0 : 1;
+                tm.sync();
+                if (tm.lane == 0) { S.qlevel[r] = sensed; S.qactive[r] = tagged ? 0 : 1; }
+                tm.sync();
+            }
+            if (remaining > 0) rew -= k.step_pen;
         }
         rew -= k.c_col * (R)col;
         if (tm.lane == 0) {
@@ -1508,7 +1570,38 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 if (i < N) {
                     R* o = A.io.obs + (long long)step * A.io.obs_step + (long long)(off + i) * od;
                     int c = 0;
-                    if (!forage) {
+                    if (disc) {
+                        o[0] = x[s]; o[1] = y[s]; o[2] = th[s];
+                        o[3] = lv[s] == 1 ? k.sense_r : (R)0;
+                        o[4] = lv[s] == 2 ? k.tag_r : (R)0;
+                        c = 5;
+                        for (int j = 0; j < N; ++j) {
+                            if (j == i) continue;
+                            o[c] = S.sx[j] - x[s];
+                            o[c + 1] = S.sy[j] - y[s];
+                            o[c + 2] = wrap_pi(S.sth[j] - th[s]);
+                            o[c + 3] = S.slevel[j] == 1 ? k.sense_r : (R)0;
+                            o[c + 4] = S.slevel[j] == 2 ? k.tag_r : (R)0;
+                            c += 5;
+                        }
+                        const int rbase = 5 + 5 * (k.n_max_obs - 1);
+                        for (; c < rbase; ++c) o[c] = (R)0;
+                        for (int r = 0; r < k.r_max; ++r) {
+                            if (r < n_res && S.qlevel[r]) {
+                                o[c] = S.qx[r] - x[s];
+                                o[c + 1] = S.qy[r] - y[s];
+                                o[c + 2] = (R)1;
+                                o[c + 3] = S.qactive[r] ? (R)0 : (R)1;
+                            } else if (r < n_res) {
+                                o[c] = k.xo - x[s];
+                                o[c + 1] = k.yo - y[s];
+                                o[c + 2] = o[c + 3] = (R)0;
+                            } else {
+                                o[c] = o[c + 1] = o[c + 2] = o[c + 3] = (R)0;
+                            }
+                            c += 4;
+                        }
+                    } else if (!forage) {
                         o[0] = x[s]; o[1] = y[s]; o[2] = th[s]; o[3] = gx[s]; o[4] = gy[s];
                         c = 5;
                         for (int j = 0; j < N; ++j) {
@@ -1566,7 +1659,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
             A.s.gth[off + i] = gth[s];
         }
     }
-    if (forage) {
+    if (resv) {
         for (int r = tm.lane; r < k.r_max; r += G) {
             A.s.qx[e * k.r_max + r] = S.qx[r];
             A.s.qy[e * k.r_max + r] = S.qy[r];
@@ -1577,7 +1670,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
     if (tm.lane == 0) {
         A.s.t[e] = t;
         A.s.ep[e] = ep;
-        if (forage) A.s.n_res[e] = n_res;
+        if (resv) A.s.n_res[e] = n_res;
 #pragma unroll
         for (int c = 0; c < kNCount; ++c) A.s.counters[e * kNCount + c] = cnt[c];
     }
@@ -1608,7 +1701,7 @@ __device__ void reset_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R,
             A.s.level[off + i] = lv;
         }
     }
-    if (A.k.scenario == 1) {
+    if (A.k.scenario != 0) {
         for (int r = tm.lane; r < A.k.r_max; r += G) {
             A.s.qx[e * A.k.r_max + r] = S.qx[r];
             A.s.qy[e * A.k.r_max + r] = S.qy[r];

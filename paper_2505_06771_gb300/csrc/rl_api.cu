@@ -86,13 +86,14 @@ rl_status cuda_fail(rl_env* h, cudaError_t e, const char* where) {
 }
 
 bool valid_cfg(const rl_config& c, std::string& why) {
-    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING) { why = "scenario"; return false; }
+    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING &&
+        c.scenario != RL_SCEN_DISCOVERY) { why = "scenario"; return false; }
     if (c.precision != RL_PREC_F32 && c.precision != RL_PREC_F64) { why = "precision"; return false; }
     if (c.episode_len < 1) { why = "episode_len"; return false; }
     if (c.max_attempts < 1) { why = "max_attempts"; return false; }
     if (!(c.l > 0) || !(c.vmax > 0) || !(c.wmax > 0) || !(c.dt > 0) || !(c.r >= 0)) { why = "constants"; return false; }
     if (!(c.xmax > c.xmin) || !(c.ymax > c.ymin)) { why = "arena"; return false; }
-    if (c.scenario == RL_SCEN_FORAGING) {
+    if (c.scenario != RL_SCEN_NAVIGATION) {
         if (c.r_max < 1 || c.r_max > rl::kMaxRes) { why = "r_max"; return false; }
         if (c.n_res_min < 0 || c.n_res_max > c.r_max || c.n_res_min > c.n_res_max) { why = "n_res"; return false; }
     }
@@ -141,6 +142,10 @@ void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
     k.waypoint = (c.scenario == RL_SCEN_NAVIGATION && c.goal_eps > 0.0) ? 1 : 0;
     k.controller = c.controller;
     k.pk1 = (R)c.pose_k1; k.pk2 = (R)c.pose_k2; k.pk3 = (R)c.pose_k3;
+    k.sense_r = (R)c.sense_radius; k.tag_r = (R)c.tag_radius;
+    k.sense_r2 = (R)(c.sense_radius * c.sense_radius); k.tag_r2 = (R)(c.tag_radius * c.tag_radius);
+    k.sense_rew = (R)c.sense_reward; k.tag_rew = (R)c.tag_reward; k.step_pen = (R)c.step_penalty;
+    k.xo = (R)(c.xmax + (c.xmax - c.xmin)); k.yo = (R)(c.ymax + (c.ymax - c.ymin));
     k.scenario = c.scenario; k.scripted = c.scripted; k.episode_len = c.episode_len;
     k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * h->n_max + 16;
     k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = h->r_max;
@@ -313,7 +318,9 @@ extern "C" {
 
 rl_status rl_config_default(int32_t scenario, rl_config* out) {
     if (!out) return RL_ERR_ARG;
-    if (scenario != RL_SCEN_NAVIGATION && scenario != RL_SCEN_FORAGING) return RL_ERR_ARG;
+    if (scenario != RL_SCEN_NAVIGATION && scenario != RL_SCEN_FORAGING &&
+        scenario != RL_SCEN_DISCOVERY)
+        return RL_ERR_ARG;
     std::memset(out, 0, sizeof(*out));
     out->scenario = scenario;
     out->precision = RL_PREC_F32;
@@ -321,7 +328,7 @@ rl_status rl_config_default(int32_t scenario, rl_config* out) {
     out->episode_len = 100;
     out->n_res_min = 2;
     out->n_res_max = 6;
-    out->r_max = scenario == RL_SCEN_FORAGING ? 6 : 0;
+    out->r_max = scenario == RL_SCEN_NAVIGATION ? 0 : 6;
     out->n_max = 0;
     out->max_attempts = 4096;
     out->qp_max_iter = 0;
@@ -355,6 +362,11 @@ rl_status rl_config_default(int32_t scenario, rl_config* out) {
     out->pose_k1 = 1.0;
     out->pose_k2 = 2.0;
     out->pose_k3 = 1.0;
+    out->sense_radius = 0.45;
+    out->tag_radius = 0.25;
+    out->sense_reward = 1.0;
+    out->tag_reward = 5.0;
+    out->step_penalty = 0.05;
     return RL_OK;
 }
 
@@ -385,8 +397,9 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     h->total = h->h_off[n_envs];
     h->n_max = cfg->n_max > 0 ? cfg->n_max : nmax_seen;
     if (h->n_max < nmax_seen) { delete h; return RL_ERR_ARG; }
-    h->r_max = cfg->scenario == RL_SCEN_FORAGING ? cfg->r_max : 0;
-    h->obs_dim = cfg->scenario == RL_SCEN_FORAGING ? 4 + 4 * (h->n_max - 1) + 4 * h->r_max
+    h->r_max = cfg->scenario != RL_SCEN_NAVIGATION ? cfg->r_max : 0;
+    h->obs_dim = cfg->scenario == RL_SCEN_DISCOVERY ? 5 + 5 * (h->n_max - 1) + 4 * h->r_max
+               : cfg->scenario == RL_SCEN_FORAGING ? 4 + 4 * (h->n_max - 1) + 4 * h->r_max
                                                    : 5 + 3 * (h->n_max - 1);
     // segments of the state image
     const size_t E = (size_t)n_envs, T = (size_t)h->total, RM = (size_t)h->r_max * E;
@@ -836,7 +849,7 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 size_t request_bytes(const rl_config& c, const rl_request& r) {
     const size_t E = (size_t)r.n_envs, rows = E * (size_t)r.n_robots;
     const size_t es = c.precision == RL_PREC_F64 ? 8 : 4;
-    const size_t RM = c.scenario == RL_SCEN_FORAGING ? E * (size_t)c.r_max : 0;
+    const size_t RM = c.scenario != RL_SCEN_NAVIGATION ? E * (size_t)c.r_max : 0;
     auto a = [](size_t v) { return (v + 255) & ~(size_t)255; };
     return 6 * a(rows * es) + a(rows * 4) + 3 * a(E * 4) + 2 * a(RM * es) + 2 * a(RM * 4) +
            a(E * rl::kNCount * 4) + a(E * 4) + a((E + 1) * 4) + a(E * 4) + a(E * es) + 4096;

@@ -56,7 +56,7 @@ template <typename R>
 rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs, void* rew,
               uint8_t* done, cudaStream_t st, unsigned char* base) {
     const int n_max = c.n_max > 0 ? c.n_max : N;
-    const int r_max = c.scenario == RL_SCEN_FORAGING ? c.r_max : 0;
+    const int r_max = c.scenario != RL_SCEN_NAVIGATION ? c.r_max : 0;
     const size_t rows = (size_t)E * N, RM = (size_t)E * r_max, es = sizeof(R);
     // state segments, each 256-byte aligned
     size_t pos = 0;
@@ -83,7 +83,8 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     a.s.nrob = nrob;
     a.s.off = off;
 
-    const int od = c.scenario == RL_SCEN_FORAGING ? 4 + 4 * (n_max - 1) + 4 * r_max
+    const int od = c.scenario == RL_SCEN_DISCOVERY ? 5 + 5 * (n_max - 1) + 4 * r_max
+                 : c.scenario == RL_SCEN_FORAGING ? 4 + 4 * (n_max - 1) + 4 * r_max
                                                   : 5 + 3 * (n_max - 1);
     a.io.E = E;
     a.io.obs_dim = od;
@@ -100,6 +101,10 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     k.waypoint = (c.scenario == RL_SCEN_NAVIGATION && c.goal_eps > 0.0) ? 1 : 0;
     k.controller = c.controller;
     k.pk1 = (R)c.pose_k1; k.pk2 = (R)c.pose_k2; k.pk3 = (R)c.pose_k3;
+    k.sense_r = (R)c.sense_radius; k.tag_r = (R)c.tag_radius;
+    k.sense_r2 = (R)(c.sense_radius * c.sense_radius); k.tag_r2 = (R)(c.tag_radius * c.tag_radius);
+    k.sense_rew = (R)c.sense_reward; k.tag_rew = (R)c.tag_reward; k.step_pen = (R)c.step_penalty;
+    k.xo = (R)(c.xmax + (c.xmax - c.xmin)); k.yo = (R)(c.ymax + (c.ymax - c.ymin));
     k.scenario = c.scenario; k.scripted = 1; k.episode_len = c.episode_len;
     k.max_iter = c.qp_max_iter > 0 ? c.qp_max_iter : 8 * n_max + 16;
     k.n_res_min = c.n_res_min; k.n_res_max = c.n_res_max; k.r_max = r_max;
@@ -161,7 +166,7 @@ extern "C" size_t rl_noalloc_state_bytes(const rl_config* c, int32_t n_envs, int
     if (!c || n_envs < 1 || n_robots < 1) return 0;
     const size_t E = (size_t)n_envs, rows = E * (size_t)n_robots;
     const size_t es = c->precision == RL_PREC_F64 ? 8 : 4;
-    const size_t RM = c->scenario == RL_SCEN_FORAGING ? E * (size_t)c->r_max : 0;
+    const size_t RM = c->scenario != RL_SCEN_NAVIGATION ? E * (size_t)c->r_max : 0;
     return 6 * align256(rows * es) + align256(rows * 4) + 3 * align256(E * 4) +
            2 * align256(RM * es) + 2 * align256(RM * 4) + align256(E * rl::kNCount * 4) +
            align256(E * 4) + align256((E + 1) * 4);
@@ -172,11 +177,13 @@ extern "C" rl_status rl_rollout_noalloc(const rl_config* cfg, int32_t n_envs, in
                                         void* d_rew_traj, uint8_t* d_done_traj, void* stream) {
     if (!cfg || n_envs < 1 || n_robots < 1 || n_robots > rl::kMaxRobots || T < 0) return RL_ERR_ARG;
     const rl_config& c = *cfg;
-    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING) return RL_ERR_ARG;
+    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING &&
+        c.scenario != RL_SCEN_DISCOVERY)
+        return RL_ERR_ARG;
     if (c.precision != RL_PREC_F32 && c.precision != RL_PREC_F64) return RL_ERR_ARG;
     if (!c.scripted || c.episode_len < 1 || c.max_attempts < 1) return RL_ERR_ARG;
     if (c.n_max != 0 && c.n_max < n_robots) return RL_ERR_ARG;
-    if (c.scenario == RL_SCEN_FORAGING &&
+    if (c.scenario != RL_SCEN_NAVIGATION &&
         (c.r_max < 1 || c.r_max > rl::kMaxRes || c.n_res_min < 0 || c.n_res_max > c.r_max ||
          c.n_res_min > c.n_res_max))
         return RL_ERR_ARG;

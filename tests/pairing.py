@@ -52,6 +52,8 @@ def obs_angle_columns(scenario, n_max, r_max):
     """Observation columns that hold angles (compared modulo 2 pi)."""
     if scenario == 0:
         return [2] + [5 + 3 * s + 2 for s in range(n_max - 1)]
+    if scenario == 2:
+        return [2] + [5 + 5 * s + 2 for s in range(n_max - 1)]
     return [2] + [4 + 4 * s + 2 for s in range(n_max - 1)]
 
 

@@ -56,7 +56,7 @@ def _check_reset_state(g, o, st, n_robots, seed):
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-@pytest.mark.parametrize("case", ["nav4", "nav20_near", "forage_uneven", "nav_edge"])
+@pytest.mark.parametrize("case", ["nav4", "nav20_near", "forage_uneven", "nav_edge", "disc_uneven"])
 def test_reset_sampler_bit_exact(rl, prec, case):
     if case == "nav4":
         g, o = make_pair(0, 4, prec)
@@ -67,6 +67,9 @@ def test_reset_sampler_bit_exact(rl, prec, case):
     elif case == "forage_uneven":
         g, o = make_pair(1, 10, prec)
         n = list(np.random.default_rng(5).integers(2, 11, 257))
+    elif case == "disc_uneven":
+        g, o = make_pair(2, 10, prec)
+        n = list(np.random.default_rng(6).integers(1, 11, 130))
     else:
         g, o = make_pair(0, 32, prec)
         n = [1, 2, 3, 5, 8, 9, 16, 17, 31, 32, 4]
@@ -122,6 +125,7 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
         assert np.array_equal(st2["gth"].astype(np.float64), s.gth), f"goal headings differ at {t}"
         if o["r_max"] > 0:
             assert np.array_equal(st2["qactive"], s.qactive), f"resources differ at step {t}"
+            assert np.array_equal(st2["qlevel"], s.qlevel), f"resource levels differ at {t}"
         cg, co = st2["counters"], s.counters.reshape(-1, 8)
         for c in (0, 1, 2, 6):
             assert np.array_equal(cg[:, c], co[:, c]), f"counter {c} differs at step {t}"
@@ -133,7 +137,7 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
 
 
 @pytest.mark.parametrize("case", ["nav4_scripted", "nav4_policy", "nav10", "forage_uneven",
-                                  "nav20_near"])
+                                  "nav20_near", "disc4", "disc_uneven"])
 def test_teacher_forced_binary32(rl, case):
     seed = 77
     if case == "nav4_scripted":
@@ -148,6 +152,12 @@ def test_teacher_forced_binary32(rl, case):
     elif case == "forage_uneven":
         g, o = make_pair(1, 10, episode_len=30)
         n, steps, act = list(np.random.default_rng(2).integers(2, 11, 200)), 40, False
+    elif case == "disc4":
+        g, o = make_pair(2, 4, episode_len=30)
+        n, steps, act = [4] * 300, 40, False
+    elif case == "disc_uneven":
+        g, o = make_pair(2, 10, episode_len=30)
+        n, steps, act = list(np.random.default_rng(4).integers(1, 11, 200)), 40, False
     else:
         g, o = make_pair(0, 20, near_frac=0.3)
         n, steps, act = [20] * 40, 25, False
@@ -247,10 +257,11 @@ def test_teacher_forced_pose_controller(rl, case):
     assert err["rew"] < 1e-5 * tol and err["obs"] < 1e-5 * tol
 
 
-def test_teacher_forced_binary64(rl):
-    g, o = make_pair(0, 4, 64)
-    err, _ = _teacher_forced(rl, g, o, [4] * 64, 5, 30)
-    print(f"\nfp64 teacher-forced: {err}")
+@pytest.mark.parametrize("scenario", [0, 2])
+def test_teacher_forced_binary64(rl, scenario):
+    g, o = make_pair(scenario, 4, 64, episode_len=30)
+    err, _ = _teacher_forced(rl, g, o, [4] * 64, 5, 40)
+    print(f"\nfp64 teacher-forced, scenario {scenario}: {err}")
     for k, v in err.items():
         assert v < 1e-11, (k, v)
 
@@ -413,7 +424,7 @@ def test_nonfinite_action_zeroed_and_reported(rl, n_robots):
     ref.close()
 
 
-@pytest.mark.parametrize("scenario", [0, 1])
+@pytest.mark.parametrize("scenario", [0, 1, 2])
 def test_uneven_one_launch_matches_steps(rl, scenario):
     """Uneven robot counts (2..10, every class up to 16 robots) in one persistent launch match
     one step at a time through the per-class launches: done flags and integer state exactly,
