@@ -86,7 +86,8 @@ def _args():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="nav", choices=list(WORKLOADS) + ["serving"])
+    p.add_argument("--workload", default="nav", choices=list(WORKLOADS) + ["serving", "policy"])
+    p.add_argument("--hidden", type=int, default=128, help="policy: GRU width (App. A: 128-512)")
     p.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form leg")
@@ -123,12 +124,15 @@ def _ncu_traffic(workload: str):
     return float(m.group(1))
 
 
-def _peaks():
+def _peaks(key: str = "hbm_gbs", fallback: float = 6800.0):
+    """A measured peak (HBM GB/s, bf16 TFLOP/s) or the fallback figure."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as fh:
-            return json.load(fh).get("hbm_gbs", 6800.0), "measured"
-    return 6800.0, "fallback"
+            d = json.load(fh)
+        if key in d:
+            return float(d[key]), "measured"
+    return fallback, "fallback"
 
 
 class Clocks:
@@ -525,12 +529,81 @@ def run_serving(a):
         print(json.dumps(line), flush=True)
 
 
+def run_policy(a):
+    """Policy in the loop: Navigation 4096 envs x 4 robots x 1000 steps driven by an MLP -> GRU
+    -> linear policy evaluated on the GPU between steps (two tensor-core GEMMs per step)."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06771_gb300 as rl
+    from synth_inputs import policy_weights
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    E, N, T, H = 4096, 4, (a.horizon or 1000), a.hidden
+    stream = torch.cuda.Stream()
+    g = rl.config_default(0, scripted=0, n_max=N)
+    with torch.cuda.stream(stream):
+        env = rl.Env(g, E, N, seed=1000 + rank, stream=stream)
+        R, od = env.total_robots, env.obs_dim
+        pol = rl.Policy(env, policy_weights(7, H, od))
+        obs0 = torch.empty(R, od, device="cuda")
+        obs = torch.empty(T, R, od, device="cuda")
+        rew = torch.empty(T, E, device="cuda")
+        done = torch.empty(T, E, dtype=torch.uint8, device="cuda")
+    env.observe(obs0)
+    stream.synchronize()
+    n_warm = max(3, a.warmup)
+    for _ in range(n_warm):
+        pol.rollout(T, obs0, obs, done, reward=rew)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    with Clocks(_gpu_index(local)) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(a.steps):
+            ev[i][0].record(stream)
+            pol.rollout(T, obs0, obs, done, reward=rew)
+            ev[i][1].record(stream)
+        t1.record(stream)
+        stream.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    per = [s.elapsed_time(e) for s, e in ev]
+    value = E * T * a.steps / (total_ms / 1e3)
+    odp = (od + 15) // 16 * 16
+    flops = 2.0 * T * R * (H * odp + 4 * H * 2 * H)  # the two GEMMs of every step
+    peak, src = _peaks(key="bf16_tflops_sustained", fallback=1700.0)
+    achieved = flops / (statistics.mean(per) / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": n_warm, "ms_per_step": total_ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": f"policy in the loop: navigation {E} envs x {N} robots x {T} "
+                                   f"steps, MLP(ReLU, {H}) -> GRU({H}) -> linear policy between "
+                                   "steps (tensor-core GEMMs via cuBLASLt, bf16 operands)",
+                       "n_envs": E, "horizon": T, "hidden": H},
+            "latency_ms": {"p50": float(np.percentile(per, 50)),
+                           "p99": float(np.percentile(per, 99))},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "kernel": "the policy's two GEMMs per step, over the whole rollout time",
+                         "flops_per_rollout": flops},
+            "e2e": None, "gpu_launches": a.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    pol.close()
+    env.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "serving":
         run_serving(a)
+    elif a.workload == "policy":
+        run_policy(a)
     else:
         run_rollout(a)
 

@@ -268,6 +268,42 @@ rl_status rl_server_drain(rl_server* srv, double timeout_s);
 /* Stop the engine, wait for running requests, free everything.  NULL-safe. */
 rl_status rl_server_destroy(rl_server* srv);
 
+/* ---- Policy in the loop ------------------------------------------------------------------
+   A recurrent policy evaluated on the GPU between steps, of the shape the paper trains (App. A:
+   a one-layer MLP with ReLU, a GRU, a linear layer; widths 128-512):
+       h1 = ReLU(W1 o + b1),  GRU(h1, h) -> h,  a = v_max tanh(Wo h + bo)
+   with the GRU's gates r = sigma(Wi_r h1 + bi_r + Wh_r h + bh_r), z (likewise) and
+   n = tanh(Wi_n h1 + bi_n + r * (Wh_n h + bh_n)), h <- (1 - z) n + z h.  The action a is the
+   robot's SI velocity (rl_step's policy actions).  The two dense layers before the gates run
+   on the tensor cores (cuBLASLt, bf16 operands: W1, b1, Wi, Wh and the inputs o, h1 and the
+   previous h are rounded to bf16, accumulation in binary32); gates, state and the head are
+   binary32.  The recurrent state is per robot, reset to zero when its env's episode ends.
+   Binary32 handles with policy actions (scripted = 0) only. */
+typedef struct rl_policy rl_policy;
+
+/* hidden: H, a multiple of 32 up to 512.  Host arrays, row-major: h_w1 [H][obs_dim], h_b1 [H],
+   h_wi [3H][H], h_bi [3H], h_wh [3H][H], h_bh [3H] (gate blocks in the order r, z, n),
+   h_wo [2][H], h_bo [2].  Copies the weights to the device; the recurrent state starts at 0. */
+rl_status rl_policy_create(rl_env* env, int32_t hidden, const float* h_w1, const float* h_b1,
+                           const float* h_wi, const float* h_bi, const float* h_wh,
+                           const float* h_bh, const float* h_wo, const float* h_bo,
+                           rl_policy** out);
+/* Zero the recurrent state of every robot. */
+rl_status rl_policy_reset_hidden(rl_policy* pol);
+/* T policy-driven steps of every env, captured once in a CUDA graph and replayed: observation
+   -> policy -> action -> rl_step.  d_obs0 [rows][obs_dim]: the observation of the current state
+   (rl_observe, or the last step's).  d_obs_traj [T][rows][obs_dim] and d_done_traj [T][E] are
+   required (step t's observation and done flags feed step t + 1); d_rew_traj [T][E] and
+   d_act_traj [T][rows][2] may be NULL. */
+rl_status rl_policy_rollout(rl_env* env, rl_policy* pol, int32_t T, const void* d_obs0,
+                            void* d_obs_traj, void* d_rew_traj, uint8_t* d_done_traj,
+                            void* d_act_traj);
+void      rl_policy_destroy(rl_policy* pol);   /* NULL-safe; waits for the handle's stream */
+
+/* The observation of the current state without stepping ([rows][obs_dim], binary32 Navigation
+   handles; RL_ERR_ARG otherwise). */
+rl_status rl_observe(rl_env* env, void* d_obs);
+
 int32_t     rl_obs_dim(const rl_env* env);
 int32_t     rl_n_envs(const rl_env* env);
 int32_t     rl_total_robots(const rl_env* env);

@@ -19,7 +19,7 @@ import numpy as np
 from .build import LIB as LIB_PATH
 from .build import build
 
-__all__ = ["build", "lib", "config_default", "Env", "Server", "RLError", "NAVIGATION",
+__all__ = ["build", "lib", "config_default", "Env", "Server", "Policy", "RLError", "NAVIGATION",
            "FORAGING", "DISCOVERY", "COUNTERS", "exported_symbols", "rollout_noalloc", "noalloc_state_bytes"]
 
 NAVIGATION, FORAGING, DISCOVERY = 0, 1, 2
@@ -126,6 +126,12 @@ def lib():
                                          vp]
         L.rl_noalloc_state_bytes.argtypes = [ctypes.POINTER(RLConfig), i32, i32]
         L.rl_noalloc_state_bytes.restype = sz
+        L.rl_policy_create.argtypes = [vp, i32] + [vp] * 8 + [ctypes.POINTER(vp)]
+        L.rl_policy_reset_hidden.argtypes = [vp]
+        L.rl_policy_rollout.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+        L.rl_policy_destroy.argtypes = [vp]
+        L.rl_policy_destroy.restype = None
+        L.rl_observe.argtypes = [vp, vp]
         _LIB = L
         return L
 
@@ -289,6 +295,12 @@ class Env:
     def sync(self):
         self._check(self._L.rl_sync(self._h), "rl_sync")
 
+    def observe(self, obs):
+        """rl_observe: the observation of the current state into obs [rows, obs_dim]."""
+        self._check(self._L.rl_observe(self._h, _dptr(obs, self.dtype,
+                                                       self.total_robots * self.obs_dim, "obs")),
+                    "rl_observe")
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.rl_destroy(self._h)
@@ -304,6 +316,58 @@ class Env:
     def state_arrays(self, blob: bytes | None = None) -> dict:
         """Parse a state blob (header + image of 256-byte-aligned segments) into arrays."""
         return parse_state(blob if blob is not None else self.get_state())
+
+
+class Policy:
+    """rl_policy_*: an MLP (ReLU) -> GRU -> linear policy evaluated on the GPU between steps of
+    a policy-driven binary32 handle.  weights: dict of float32 arrays w1 [H, obs_dim], b1 [H],
+    wi [3H, H], bi [3H], wh [3H, H], bh [3H] (gates r, z, n), wo [2, H], bo [2]."""
+
+    NAMES = ("w1", "b1", "wi", "bi", "wh", "bh", "wo", "bo")
+
+    def __init__(self, env: "Env", weights: dict):
+        self._L = lib()
+        self.env = env
+        H = int(np.asarray(weights["b1"]).shape[0])
+        self.hidden = H
+        self._w = [np.ascontiguousarray(weights[k], dtype=np.float32) for k in self.NAMES]
+        h = ctypes.c_void_p()
+        st = self._L.rl_policy_create(env._h, H, *[a.ctypes.data for a in self._w],
+                                      ctypes.byref(h))
+        if st != 0:
+            raise RLError(st, "rl_policy_create: " + self._L.rl_last_error(env._h).decode())
+        self._h = h
+
+    def reset_hidden(self):
+        st = self._L.rl_policy_reset_hidden(self._h)
+        if st != 0:
+            raise RLError(st, "rl_policy_reset_hidden")
+
+    def rollout(self, T: int, obs0, obs, done, reward=None, actions=None):
+        """T policy-driven steps: obs0 [rows, od] -> obs [T, rows, od], done [T, E], reward
+        [T, E] and actions [T, rows, 2] (optional)."""
+        import torch
+        e = self.env
+        R, E, od = e.total_robots, e.n_envs, e.obs_dim
+        st = self._L.rl_policy_rollout(
+            e._h, self._h, T, _dptr(obs0, torch.float32, R * od, "obs0"),
+            _dptr(obs, torch.float32, T * R * od, "obs"),
+            _dptr(reward, torch.float32, T * E, "reward"),
+            _dptr(done, torch.uint8, T * E, "done"),
+            _dptr(actions, torch.float32, T * R * 2, "actions"))
+        if st != 0:
+            raise RLError(st, "rl_policy_rollout: " + self._L.rl_last_error(e._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rl_policy_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rollout_noalloc(cfg: dict, n_envs: int, n_robots: int, seed: int, T: int, obs=None,

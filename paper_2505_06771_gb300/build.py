@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librobo_gb300.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["rl_api.cu", "kernels_f32_small.cu", "kernels_f32_large.cu", "kernels_f64.cu",
-           "rl_noalloc.cu", "kernels_multi.cu"]
+           "rl_noalloc.cu", "kernels_multi.cu", "policy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -62,7 +62,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     if force or _stale(objs, LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcublasLt"],
+                       check=True)
         os.replace(tmp, LIB)
     return LIB
 

@@ -1,0 +1,20 @@
+// internal.h -- what the policy module needs to know about a handle (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rl.h"
+#include "env_step.cuh"
+
+namespace rl {
+
+cudaStream_t env_stream(const rl_env* h);
+const std::vector<int32_t>& env_offsets(const rl_env* h);  // [E + 1] first row of each env
+const rl_config& env_config(const rl_env* h);
+void env_set_error(rl_env* h, const std::string& msg);
+// The launch arguments of a binary32 handle (state views, constants); false for binary64.
+bool env_args_f32(const rl_env* h, LaunchArgs<float>& a);
+
+}  // namespace rl

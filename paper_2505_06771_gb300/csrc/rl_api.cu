@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/rl.h"
+#include "internal.h"
 #include "launch.h"
 
 namespace {
@@ -73,6 +74,26 @@ struct rl_env {
     // device status word (rl::kStatusNonFiniteAction ...), read by the synchronising calls
     int32_t* d_status = nullptr;
 };
+
+namespace rl {
+cudaStream_t env_stream(const rl_env* h) { return h->st; }
+const std::vector<int32_t>& env_offsets(const rl_env* h) { return h->h_off; }
+const rl_config& env_config(const rl_env* h) { return h->cfg; }
+void env_set_error(rl_env* h, const std::string& msg) { h->err = msg; }
+}  // namespace rl
+
+namespace {
+template <typename R>
+void fill_args(const rl_env* h, rl::LaunchArgs<R>& a);
+}  // namespace
+
+namespace rl {
+bool env_args_f32(const rl_env* h, LaunchArgs<float>& a) {
+    if (h->prec != 32) return false;
+    fill_args<float>(h, a);
+    return true;
+}
+}  // namespace rl
 
 namespace {
 

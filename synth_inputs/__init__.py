@@ -21,6 +21,18 @@ def policy_actions(seed: int, step: int, total_robots: int, amp: float = 0.3,
     return rng.uniform(-amp, amp, (total_robots, 2)).astype(dtype)
 
 
+def policy_weights(seed: int, hidden: int, obs_dim: int) -> dict:
+    """Weights of the MLP -> GRU -> linear policy, each layer uniform in +-1/sqrt(fan_in)."""
+    g = np.random.default_rng(seed)
+    s1, s2 = 1.0 / np.sqrt(obs_dim), 1.0 / np.sqrt(hidden)
+    H = hidden
+    w = dict(w1=g.uniform(-s1, s1, (H, obs_dim)), b1=g.uniform(-s1, s1, H),
+             wi=g.uniform(-s2, s2, (3 * H, H)), bi=g.uniform(-s2, s2, 3 * H),
+             wh=g.uniform(-s2, s2, (3 * H, H)), bh=g.uniform(-s2, s2, 3 * H),
+             wo=g.uniform(-s2, s2, (2, H)), bo=g.uniform(-0.1, 0.1, 2))
+    return {k: v.astype(np.float32) for k, v in w.items()}
+
+
 def serving_requests(seed: int, duration_s: float, rate_hz: float = 200.0,
                      envs_max: int = 2048, robots_lo: int = 2, robots_hi: int = 12,
                      horizon_lo: int = 100, horizon_hi: int = 1000) -> list[dict]:
