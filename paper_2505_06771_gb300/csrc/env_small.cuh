@@ -565,20 +565,22 @@ static __device__ __noinline__ void small_disc_obs(const TeamSmem<float, 4>& S, 
 
 // One env of at most 4 robots for T steps (team of 4 lanes).  FAST: the Navigation scenario with
 // scripted nominal control and no traces, every such branch folded away at compile time.
-template <bool FAST>
+// SCEN >= 0 fixes the scenario at compile time and LEAN drops policy actions and traces (the
+// one-launch kernel's scripted rollouts).
+template <bool FAST, int SCEN = -1, bool LEAN = false>
 __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
                               TeamSmem<float, 4>& S, int e) {
     const StepConsts<float>& k = A.k;
     const int off = A.s.off[e];
     const int N = A.s.nrob[e];
-    const bool forage = !FAST && (k.scenario == 1);
-    const bool disc = !FAST && (k.scenario == 2);
+    const bool forage = !FAST && ((SCEN < 0) ? (k.scenario == 1) : (SCEN == 1));
+    const bool disc = !FAST && ((SCEN < 0) ? (k.scenario == 2) : (SCEN == 2));
     const bool resv = forage || disc;  // per-env resources / landmarks
-    const float* actions = FAST ? nullptr : A.io.actions;
-    float* tr_unom = FAST ? nullptr : A.io.u_nom;
-    float* tr_ustar = FAST ? nullptr : A.io.u_star;
-    float* tr_vw = FAST ? nullptr : A.io.vw;
-    int32_t* tr_qp = FAST ? nullptr : A.io.qp_info;
+    const float* actions = (FAST || LEAN) ? nullptr : A.io.actions;
+    float* tr_unom = (FAST || LEAN) ? nullptr : A.io.u_nom;
+    float* tr_ustar = (FAST || LEAN) ? nullptr : A.io.u_star;
+    float* tr_vw = (FAST || LEAN) ? nullptr : A.io.vw;
+    int32_t* tr_qp = (FAST || LEAN) ? nullptr : A.io.qp_info;
     const int i = tm.lane;
     const bool own = i < N;
     const int row = off + (own ? i : 0);

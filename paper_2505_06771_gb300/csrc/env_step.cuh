@@ -1220,15 +1220,23 @@ __device__ __forceinline__ bool discovery_target(const R* qx, const R* qy, const
 // ------------------------------------------------------------------------------------------
 // One env for T steps
 // ------------------------------------------------------------------------------------------
-template <typename R, int G, int NMAX>
+// SCEN >= 0 fixes the scenario at compile time and LEAN drops policy actions and traces (a
+// scripted rollout): the one-launch kernel instantiates the step it needs, nothing more, which
+// keeps its code -- every class's loop in one kernel -- small for the instruction cache.
+template <typename R, int G, int NMAX, int SCEN = -1, bool LEAN = false>
 __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, NMAX>& S, int e) {
     constexpr int RPL = (NMAX + G - 1) / G;
     const StepConsts<R>& k = A.k;
     const int off = A.s.off[e];
     const int N = A.s.nrob[e];
-    const bool forage = (k.scenario == 1);
-    const bool disc = (k.scenario == 2);
+    const bool forage = (SCEN < 0) ? (k.scenario == 1) : (SCEN == 1);
+    const bool disc = (SCEN < 0) ? (k.scenario == 2) : (SCEN == 2);
     const bool resv = forage || disc;  // per-env resources / landmarks
+    const R* actions = LEAN ? nullptr : A.io.actions;
+    R* tr_unom = LEAN ? nullptr : A.io.u_nom;
+    R* tr_ustar = LEAN ? nullptr : A.io.u_star;
+    R* tr_vw = LEAN ? nullptr : A.io.vw;
+    int32_t* tr_qp = LEAN ? nullptr : A.io.qp_info;
     QPWork<R, NMAX>& W = WorkSel<R, NMAX>::get(S.qp);
 
     QPConsts<R> qc;
@@ -1283,9 +1291,9 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
             if (i < N) {
                 const R px = x[s] + k.l * cs[s], py = y[s] + k.l * sn[s];
                 R ux, uy;
-                if (A.io.actions) {
-                    ux = A.io.actions[2 * (off + i)];
-                    uy = A.io.actions[2 * (off + i) + 1];
+                if (actions) {
+                    ux = actions[2 * (off + i)];
+                    uy = actions[2 * (off + i) + 1];
                     screen_action(A.io.status, ux, uy);
                 } else {
                     R tx = gx[s], ty = gy[s];
@@ -1400,17 +1408,17 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 wl = fmin(fmax(wl, -k.vmax), k.vmax);
                 v = (R)0.5 * (wr + wl);
                 om = (wr - wl) * k.inv_track;
-                if (A.io.u_nom) {
-                    A.io.u_nom[2 * (off + i)] = u0x[s];
-                    A.io.u_nom[2 * (off + i) + 1] = u0y[s];
+                if (tr_unom) {
+                    tr_unom[2 * (off + i)] = u0x[s];
+                    tr_unom[2 * (off + i) + 1] = u0y[s];
                 }
-                if (A.io.u_star) {
-                    A.io.u_star[2 * (off + i)] = usx[s];
-                    A.io.u_star[2 * (off + i) + 1] = usy[s];
+                if (tr_ustar) {
+                    tr_ustar[2 * (off + i)] = usx[s];
+                    tr_ustar[2 * (off + i) + 1] = usy[s];
                 }
-                if (A.io.vw) {
-                    A.io.vw[2 * (off + i)] = v;
-                    A.io.vw[2 * (off + i) + 1] = om;
+                if (tr_vw) {
+                    tr_vw[2 * (off + i)] = v;
+                    tr_vw[2 * (off + i) + 1] = om;
                 }
                 x[s] += k.dt * v * cs[s];
                 y[s] += k.dt * v * sn[s];
@@ -1523,11 +1531,11 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
             cnt[5] += (res.status == 1) ? 1 : 0;
             cnt[7] += res.iters;
         }
-        if (A.io.qp_info && tm.lane == 0) {
-            A.io.qp_info[4 * e + 0] = res.status;
-            A.io.qp_info[4 * e + 1] = res.q;
-            A.io.qp_info[4 * e + 2] = res.iters;
-            A.io.qp_info[4 * e + 3] = qflags;
+        if (tr_qp && tm.lane == 0) {
+            tr_qp[4 * e + 0] = res.status;
+            tr_qp[4 * e + 1] = res.q;
+            tr_qp[4 * e + 2] = res.iters;
+            tr_qp[4 * e + 3] = qflags;
         }
 
         // ---- episode end and auto-reset

@@ -10,10 +10,12 @@
 
 namespace rl {
 
-__global__ void __launch_bounds__(64) env_kernel_multi(MultiArgs M) {
+// SCEN: the batch's scenario, fixed at compile time (Navigation takes the gather fast path for
+// its 4-robot class; the others the lean scripted steps).
+template <int SCEN>
+__global__ void __launch_bounds__(64, 1) env_kernel_multi(MultiArgs M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    const bool fast = M.fast;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(M.head, 1u);
         __syncthreads();
@@ -29,8 +31,8 @@ __global__ void __launch_bounds__(64) env_kernel_multi(MultiArgs M) {
                 const int tib = threadIdx.x / 4;
                 TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + tib;
                 if (tib < w.z) {
-                    if (fast) run_env_nav4(M.a, tm, *S, list[tib]);
-                    else run_env_small<false>(M.a, tm, *S, list[tib]);
+                    if constexpr (SCEN == 0) run_env_nav4(M.a, tm, *S, list[tib]);
+                    else run_env_small<false, SCEN, true>(M.a, tm, *S, list[tib]);
                 }
                 break;
             }
@@ -38,28 +40,28 @@ __global__ void __launch_bounds__(64) env_kernel_multi(MultiArgs M) {
                 const Team<8> tm;
                 const int tib = threadIdx.x / 8;
                 TeamSmem<float, 8>* S = reinterpret_cast<TeamSmem<float, 8>*>(smem_raw) + tib;
-                if (tib < w.z) run_env<float, 8, 8>(M.a, tm, *S, list[tib]);
+                if (tib < w.z) run_env<float, 8, 8, SCEN, true>(M.a, tm, *S, list[tib]);
                 break;
             }
             case 16: {
                 const Team<16> tm;
                 const int tib = threadIdx.x / 16;
                 TeamSmem<float, 16>* S = reinterpret_cast<TeamSmem<float, 16>*>(smem_raw) + tib;
-                if (tib < w.z) run_env<float, 16, 16>(M.a, tm, *S, list[tib]);
+                if (tib < w.z) run_env<float, 16, 16, SCEN, true>(M.a, tm, *S, list[tib]);
                 break;
             }
             case 20: {
                 const Team<32> tm;
                 const int tib = threadIdx.x / 32;
                 TeamSmem<float, 20>* S = reinterpret_cast<TeamSmem<float, 20>*>(smem_raw) + tib;
-                if (tib < w.z) run_env<float, 32, 20>(M.a, tm, *S, list[tib]);
+                if (tib < w.z) run_env<float, 32, 20, SCEN, true>(M.a, tm, *S, list[tib]);
                 break;
             }
             default: {
                 const Team<32> tm;
                 const int tib = threadIdx.x / 32;
                 TeamSmem<float, 32>* S = reinterpret_cast<TeamSmem<float, 32>*>(smem_raw) + tib;
-                if (tib < w.z) run_env<float, 32, 32>(M.a, tm, *S, list[tib]);
+                if (tib < w.z) run_env<float, 32, 32, SCEN, true>(M.a, tm, *S, list[tib]);
                 break;
             }
         }
@@ -79,13 +81,17 @@ size_t multi_smem_bytes(unsigned class_mask) {
 
 cudaError_t launch_multi(const MultiArgs& m, unsigned class_mask, int max_blocks, cudaStream_t st) {
     const size_t smem = multi_smem_bytes(class_mask);
+    const int scen = m.a.k.scenario;
+    if (scen < 0 || scen > 2) return cudaErrorInvalidValue;
+    void (*kern)(MultiArgs) = scen == 0 ? env_kernel_multi<0>
+                              : (scen == 1 ? env_kernel_multi<1> : env_kernel_multi<2>);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(env_kernel_multi,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, env_kernel_multi, 64, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, smem);
     if (e != cudaSuccess) return e;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -96,7 +102,7 @@ cudaError_t launch_multi(const MultiArgs& m, unsigned class_mask, int max_blocks
     if (blocks <= 0) return cudaSuccess;
     e = cudaMemsetAsync(m.head, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    env_kernel_multi<<<blocks, 64, smem, st>>>(m);
+    kern<<<blocks, 64, smem, st>>>(m);
     return cudaGetLastError();
 }
 
