@@ -277,7 +277,8 @@ rl_status rl_server_destroy(rl_server* srv);
    robot's SI velocity (rl_step's policy actions).  The two dense layers before the gates run
    on the tensor cores (cuBLASLt, bf16 operands: W1, b1, Wi, Wh and the inputs o, h1 and the
    previous h are rounded to bf16, accumulation in binary32); gates, state and the head are
-   binary32.  The recurrent state is per robot, reset to zero when its env's episode ends.
+   binary32, the gates' sigma and tanh from the hardware tanh approximation (relative error
+   about 2^-11).  The recurrent state is per robot, reset to zero when its env's episode ends.
    Binary32 handles with policy actions (scripted = 0) only. */
 typedef struct rl_policy rl_policy;
 

@@ -49,7 +49,14 @@ __global__ void policy_input(const float* __restrict__ obs, int rows, int od, in
     }
 }
 
-__device__ __forceinline__ float sigmoid_f(float v) { return 1.f / (1.f + expf(-v)); }
+// Gate nonlinearities on the special-function unit: tanh.approx.f32 (relative error about
+// 2^-11, below the bf16 rounding of the GEMM operands) and sigma(v) = (1 + tanh(v / 2)) / 2.
+__device__ __forceinline__ float tanh_sfu(float v) {
+    float r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float sigmoid_f(float v) { return fmaf(0.5f, tanh_sfu(0.5f * v), 0.5f); }
 
 // One warp per robot: gates from the pre-activations g [rows][4H] (r, z, n from h1, n from
 // h_prev), the new state, and a = v_max tanh(Wo h + bo).
@@ -66,7 +73,7 @@ __global__ void policy_gates(const float* __restrict__ g, const float* __restric
         for (int u = lane; u < H; u += 32) {
             const float rg = sigmoid_f(gr[u] + bias[u]);
             const float zg = sigmoid_f(gr[H + u] + bias[H + u]);
-            const float ng = tanhf(gr[2 * H + u] + bias[2 * H + u] + rg * (gr[3 * H + u] + bias[3 * H + u]));
+            const float ng = tanh_sfu(gr[2 * H + u] + bias[2 * H + u] + rg * (gr[3 * H + u] + bias[3 * H + u]));
             const float hp = h[(size_t)r * H + u];
             const float hn = (1.f - zg) * ng + zg * hp;
             h[(size_t)r * H + u] = hn;
