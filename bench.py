@@ -98,6 +98,26 @@ def _args():
     return p.parse_args()
 
 
+def _rank_seed(rank: int) -> int:
+    """Each rank runs its own batch (weak scaling): the batch's seed."""
+    return 1000 + rank
+
+
+def _max_over_ranks(dist, ms: float, device) -> float:
+    """The slowest rank's time, on every rank (the time itself with one rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def _dist():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -343,7 +363,7 @@ def run_rollout(a):
     fdt = torch.float64 if w["precision"] == 64 else torch.float32
     esz = 8 if w["precision"] == 64 else 4
     with torch.cuda.stream(stream):
-        env = rl.Env(g, E, n, seed=1000 + rank, stream=stream)
+        env = rl.Env(g, E, n, seed=_rank_seed(rank), stream=stream)
         rows = env.total_robots
         obs = torch.empty(T, rows, env.obs_dim, dtype=fdt, device="cuda")
         rew = torch.empty(T, E, dtype=fdt, device="cuda")
@@ -379,11 +399,8 @@ def run_rollout(a):
     per = [s.elapsed_time(e) for s, e in ev]
     counters = env.counters()  # since the tuner: the warm-up and timed rollouts
     env_steps_counted = E * T * (n_warm + a.steps)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = E * T * a.steps * world / (total_ms / 1e3)
+    total_ms = _max_over_ranks(dist, total_ms, "cuda")
+    value = _job_rate(E * T * a.steps, world, total_ms)
 
     # ---- roofline of the rollout kernel (the only kernel of the step)
     traj_bytes = T * (rows * env.obs_dim * esz + E * esz + E)
@@ -544,7 +561,7 @@ def run_policy(a):
     stream = torch.cuda.Stream()
     g = rl.config_default(0, scripted=0, n_max=N)
     with torch.cuda.stream(stream):
-        env = rl.Env(g, E, N, seed=1000 + rank, stream=stream)
+        env = rl.Env(g, E, N, seed=_rank_seed(rank), stream=stream)
         R, od = env.total_robots, env.obs_dim
         pol = rl.Policy(env, policy_weights(7, H, od))
         obs0 = torch.empty(R, od, device="cuda")
