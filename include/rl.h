@@ -87,7 +87,10 @@ typedef struct {
     int32_t resolve_f64;    /* 1: re-solve flagged binary32 QPs in binary64 */
     int32_t lanes;          /* lanes per environment (0: the class default or rl_tune's pick) */
     int32_t block_threads;  /* threads per block, a multiple of 32 up to 256 (0: default) */
-    int32_t warp_envs;      /* 4-robot binary32 class: envs per 32-lane warp (0: default) */
+    int32_t warp_envs;      /* 4-robot binary32 class: envs per 32-lane warp (0: default: for
+                               scripted Navigation the envs are spread evenly over one block of 4
+                               warps per SM when that leaves at most 8 per warp, else 6 per warp
+                               for the shuffle kernel and 4 otherwise) */
     int32_t small_variant;  /* 4-robot binary32 Navigation, scripted, without traces: 1 the team
                                kernel that reduces across lanes with shuffles (faster on large
                                batches), 2 the team kernel that publishes each robot's state in

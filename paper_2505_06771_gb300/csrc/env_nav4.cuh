@@ -448,13 +448,26 @@ template <int MODE>
 __global__ void __launch_bounds__(128, 1) env_kernel_small(LaunchArgs<float> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Team<4> tm;
-    const int per = (A.warp_envs >= 1 && A.warp_envs <= 8) ? A.warp_envs : 4;
     const int tiw = (threadIdx.x & 31) >> 2;  // team in warp
-    if (tiw >= per) return;
     const int tib = threadIdx.x / 4;
     TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + tib;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    if (A.warp_envs <= 0) {
+        // spread: warp w takes list entries [w n / W, (w + 1) n / W), at most 8 (the launcher
+        // guarantees it), one env per team
+        const long long n = A.n_list;
+        const int lo = (int)(warp * n / warps), hi = (int)((warp + 1) * n / warps);
+        const int idx = lo + tiw;
+        if (idx >= hi) return;
+        const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
+        if constexpr (MODE == 2) run_env_nav4(A, tm, *S, e);
+        else if constexpr (MODE == 1) run_env_small<true>(A, tm, *S, e);
+        else run_env_small<false>(A, tm, *S, e);
+        return;
+    }
+    const int per = A.warp_envs <= 8 ? A.warp_envs : 4;
+    if (tiw >= per) return;
     for (int idx = warp * per + tiw; idx < A.n_list; idx += warps * per) {
         const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
         if constexpr (MODE == 2) run_env_nav4(A, tm, *S, e);

@@ -109,7 +109,8 @@ struct LaunchArgs {
     int n_list;
     int env_begin;
     int T;
-    int warp_envs;  // one-thread-per-env kernel: envs per 32-lane warp
+    int warp_envs;  // envs per 32-lane warp; 4-robot team kernels: <= 0 spreads the envs evenly
+                    // over all warps of the grid (at most 8 per warp, one pass)
     int variant;    // 4-robot binary32 Navigation fast path: 1 shuffle team, 2 gather team
     uint64_t seed;
 };

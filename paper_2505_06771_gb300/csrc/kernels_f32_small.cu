@@ -9,6 +9,10 @@ namespace rl {
 
 static bool is_fast(const LaunchArgs<float>& a);
 
+// Dynamic shared memory of a spread launch: more than half of an SM's 228 KB, so one block
+// per SM.
+constexpr size_t kSpreadSmem = 116 * 1024;
+
 static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threads,
                                      int max_blocks, cudaStream_t st) {
     if (block_threads < 32 || block_threads % 32 != 0) return cudaErrorInvalidValue;
@@ -24,12 +28,33 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
         // envs run 10% faster with the shuffle kernel, one env 20% faster with the gather one
         variant = a.n_list <= 1024 ? 2 : 1;
     }
+    void (*kern)(LaunchArgs<float>) = !fast ? env_kernel_small<0>
+                                      : (variant == 2 ? env_kernel_small<2> : env_kernel_small<1>);
+    if (fast && a.warp_envs <= 0 && max_blocks <= 0) {
+        // Spread: one block of 4 warps per SM, so that each warp scheduler runs one warp, and
+        // the envs divided evenly over the warps (at most 8 per warp).  The kernel time is the
+        // slowest warp's: with a fixed number of envs per warp (6 on 4096 envs) some schedulers
+        // get two warps and run them at about half speed.  The shared-memory request keeps a
+        // second block off each SM.
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int blocks = std::min(sms, (a.n_list + 3) / 4);
+        if (blocks >= 1 && a.n_list <= 8 * 4 * blocks) {
+            const size_t sp = std::max((size_t)32 * sizeof(TeamSmem<float, 4>), kSpreadSmem);
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
+            if (e != cudaSuccess) return e;
+            LaunchArgs<float> b = a;
+            b.warp_envs = 0;
+            kern<<<blocks, 128, sp, st>>>(b);
+            return cudaGetLastError();
+        }
+    }
     // envs per warp: 6 for the shuffle kernel (fastest on 4096 envs: 2.60 ms against 2.71 ms
     // with 8 and 2.85 ms with 5), 4 otherwise
     const int per = (a.warp_envs >= 1 && a.warp_envs <= 8) ? a.warp_envs
                                                              : ((fast && variant == 1) ? 6 : 4);
-    void (*kern)(LaunchArgs<float>) = !fast ? env_kernel_small<0>
-                                      : (variant == 2 ? env_kernel_small<2> : env_kernel_small<1>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -179,6 +179,37 @@ __device__ __forceinline__ QPResult thread_qp(const Q (&Px)[4], const Q (&Py)[4]
         const Q app = tdot(ap, ap);
         Q lam_p = (Q)0;
         bool added = false;
+        if constexpr (CAP >= 2) if (q == 1) {
+            // The common second row, written out: with one active row the Cholesky solves are
+            // scalar, and the row is added when the full primal step is feasible (tf <= td).
+            // Otherwise (a drop, a dependent row) the general pass below takes it.
+            const Q y0 = tdot(AR[0], ap) * dinv[0];
+            const Q r0 = y0 * dinv[0];
+            Q z[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) z[m] = ap[m] - r0 * AR[0][m];
+            const Q zz = tdot(z, z);
+            const Q td = r0 > (Q)0 ? lam[0] / r0 : (Q)CUDART_INF;
+            const Q tf = (tdot(ap, U) - bp) / zz;
+            if (zz > c.eps_dep * app && tf <= td) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    U[m] -= tf * z[m];
+                    AR[1][m] = ap[m];
+                }
+                lam[0] -= tf * r0;
+                const Q dg = sqrt(zz);
+                L[1] = y0;
+                L[2] = dg;
+                dinv[1] = (Q)1 / dg;
+                lam[1] = tf;
+                hs[1] = hp;
+                slot[1] = r;
+                act |= 1u << r;
+                q = 2;
+                added = true;
+            }
+        }
         for (int guard = 0; guard <= CAP + 1 && !added; ++guard) {
             Q y[CAP], rr[CAP];
 #pragma unroll

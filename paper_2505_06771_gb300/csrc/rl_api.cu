@@ -669,7 +669,8 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
         int cand[32][4];
         int nc_ = 0;
         if (h->prec == 32 && all[c].nmax == 4) {
-            const int we4[6] = {1, 2, 4, 6, 7, 8}, we1[3] = {8, 16, 32};
+            // envs per warp; 0: spread evenly over one block per SM
+            const int we4[6] = {0, 2, 4, 6, 7, 8}, we1[3] = {8, 16, 32};
             for (int var = 1; var <= 2; ++var)
                 for (int w = 0; w < 6; ++w) {
                     cand[nc_][0] = 4; cand[nc_][1] = 128; cand[nc_][2] = we4[w]; cand[nc_][3] = var;
