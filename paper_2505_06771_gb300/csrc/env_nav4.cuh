@@ -461,8 +461,11 @@ __global__ void __launch_bounds__(128, 1) env_kernel_small(LaunchArgs<float> A) 
         const int idx = lo + tiw;
         if (idx >= hi) return;
         const int e = A.env_list ? A.env_list[idx] : A.env_begin + idx;
+        // the warp's live lanes (teams 0 .. hi - lo - 1), for the warp-wide rare QPs
+        const int nw = hi - lo;
+        const unsigned wm = nw >= 8 ? 0xffffffffu : (nw >= 2 ? (1u << (4 * nw)) - 1u : 0u);
         if constexpr (MODE == 2) run_env_nav4(A, tm, *S, e);
-        else if constexpr (MODE == 1) run_env_small<true>(A, tm, *S, e);
+        else if constexpr (MODE == 1) run_env_small<true>(A, tm, *S, e, wm);
         else run_env_small<false>(A, tm, *S, e);
         return;
     }

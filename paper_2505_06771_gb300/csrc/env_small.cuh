@@ -13,6 +13,7 @@
 #pragma once
 #include "env_step.cuh"
 #include "qp_regs.cuh"
+#include "qp_warp.cuh"
 
 namespace rl {
 
@@ -385,10 +386,12 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
 // closed-form first iteration) on the whole 8-variable QP, with no cross-lane traffic inside
 // the solve, and keeps its own robot's u.  Every lane takes the same branches, so the team
 // never diverges; an active set beyond kRegRows rows goes to the shared-memory solver.
+// defer: an active set beyond kRegRows rows is not solved here but returned as status 3 (the
+// caller hands it to the whole warp).
 __device__ __forceinline__ QPResult small_filter_all(const Team<4>& tm, TeamSmem<float, 4>& S,
                                                      int N, float px, float py, float u0x,
                                                      float u0y, const QPConsts<float>& c,
-                                                     float& usx, float& usy) {
+                                                     float& usx, float& usy, bool defer = false) {
     float Px[4], Py[4], U0[8], U[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -399,6 +402,12 @@ __device__ __forceinline__ QPResult small_filter_all(const Team<4>& tm, TeamSmem
     }
     bool overflow;
     QPResult res = thread_qp<float, kRegRows>(Px, Py, N, U0, c, U, overflow);
+    if (overflow && defer) {
+        res.status = 3;
+        usx = u0x;
+        usy = u0y;
+        return res;
+    }
     if (overflow) {
         res = small_general(tm, S, N, px, py, u0x, u0y, c);
         const int i = tm.lane;
@@ -567,9 +576,13 @@ static __device__ __noinline__ void small_disc_obs(const TeamSmem<float, 4>& S, 
 // scripted nominal control and no traces, every such branch folded away at compile time.
 // SCEN >= 0 fixes the scenario at compile time and LEAN drops policy actions and traces (the
 // one-launch kernel's scripted rollouts).
+// wm (scripted Navigation only): the lanes of the warp's live teams, all running the same steps
+// in step with each other, when there are at least two; the rare QPs (an active set beyond the
+// register solver's, the binary64 re-solve) are then solved by the whole warp (qp_warp.cuh).
+// 0: each team solves its own in shared memory.
 template <bool FAST, int SCEN = -1, bool LEAN = false>
 __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
-                              TeamSmem<float, 4>& S, int e) {
+                              TeamSmem<float, 4>& S, int e, unsigned wm = 0u) {
     const StepConsts<float>& k = A.k;
     const int off = A.s.off[e];
     const int N = A.s.nrob[e];
@@ -678,9 +691,76 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         const float dold = fast_norm(px - gx, py - gy);
         // ---- the barrier QP
         float usx, usy;
-        QPResult res = small_filter_all(tm, S, N, px, py, ux, uy, qc, usx, usy);
+        const bool by_warp = FAST && wm != 0u;
+        QPResult res = small_filter_all(tm, S, N, px, py, ux, uy, qc, usx, usy, by_warp);
         int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
-        if (k.resolve_f64 && res.flag) {
+        if (by_warp) {
+            // rare QPs of the warp's envs, one env at a time by all live lanes
+            const int nl = __popc(wm);
+            const int wl = threadIdx.x & 31;
+            unsigned need = __ballot_sync(wm, i == 0 && res.status == 3);
+            while (need) {
+                const int src = __ffs(need) - 1;  // the team's first lane
+                need &= need - 1u;
+                const int Ns = __shfl_sync(wm, N, src);
+                float Px[4], Py[4], U0[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    Px[j] = __shfl_sync(wm, px, src + j);
+                    Py[j] = __shfl_sync(wm, py, src + j);
+                    U0[2 * j] = __shfl_sync(wm, ux, src + j);
+                    U0[2 * j + 1] = __shfl_sync(wm, uy, src + j);
+                }
+                float um;
+                const QPResult r = warp_qp<float>(wm, nl, Ns, Px, Py, U0, qc, um);
+                const float ox = __shfl_sync(wm, um, 2 * (wl & 3));
+                const float oy = __shfl_sync(wm, um, 2 * (wl & 3) + 1);
+                if (tm.base == src) {
+                    res = r;
+                    usx = own ? ox : 0.f;
+                    usy = own ? oy : 0.f;
+                }
+            }
+            need = __ballot_sync(wm, i == 0 && k.resolve_f64 && res.flag);
+            if (need) {
+                // binary64: projected points from the binary32 pose, as the team re-solve
+                double sd, cd;
+                sincos((double)th, &sd, &cd);
+                const double pxd = (double)x + (double)k.l * cd;
+                const double pyd = (double)y + (double)k.l * sd;
+                QPConsts<double> dc;
+                dc.gamma = (double)k.gamma; dc.r2 = (double)k.r2; dc.kg = (double)k.kg;
+                dc.half_r = (double)k.half_r; dc.xmin = (double)k.xmin; dc.xmax = (double)k.xmax;
+                dc.ymin = (double)k.ymin; dc.ymax = (double)k.ymax; dc.h_flag = (double)k.h_flag;
+                dc.max_iter = 8 * 4 + 16;
+                dc.tol_abs = 1e-12; dc.tol_rel = 1e-12; dc.eps_dep = 1e-12; dc.tol_lam = 1e-10;
+                while (need) {
+                    const int src = __ffs(need) - 1;
+                    need &= need - 1u;
+                    const int Ns = __shfl_sync(wm, N, src);
+                    double Px[4], Py[4], U0[8];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        Px[j] = __shfl_sync(wm, pxd, src + j);
+                        Py[j] = __shfl_sync(wm, pyd, src + j);
+                        U0[2 * j] = (double)__shfl_sync(wm, ux, src + j);
+                        U0[2 * j + 1] = (double)__shfl_sync(wm, uy, src + j);
+                    }
+                    double um;
+                    const QPResult r64 = warp_qp<double>(wm, nl, Ns, Px, Py, U0, dc, um);
+                    const double ox = __shfl_sync(wm, um, 2 * (wl & 3));
+                    const double oy = __shfl_sync(wm, um, 2 * (wl & 3) + 1);
+                    if (tm.base == src) {
+                        res.status = r64.status;
+                        res.q = r64.q;
+                        res.iters += r64.iters;
+                        usx = own ? (float)ox : 0.f;
+                        usy = own ? (float)oy : 0.f;
+                        qflags |= 2;
+                    }
+                }
+            }
+        } else if (k.resolve_f64 && res.flag) {
             const QPResult r64 = small_resolve_f64(tm, S, k, N, x, y, th, ux, uy);
             res.status = r64.status;
             res.q = r64.q;

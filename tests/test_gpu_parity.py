@@ -132,6 +132,8 @@ def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
         if traces:
             qi = b["qp_info"].cpu().numpy()
             flagged += int(((qi[:, 3] >> 1) & 1).sum())
+    if not traces:
+        flagged = int(env.state_arrays()["counters"][:, 4].sum())
     env.close()
     return err, flagged
 
@@ -186,6 +188,31 @@ def test_teacher_forced_fast_kernels(rl, kern, N, E):
     g, o = make_pair(0, N, episode_len=30, **FAST_KERNELS[kern])
     err, _ = _teacher_forced(rl, g, o, [N] * E, 91, 40, traces=False)
     print(f"\n{kern} kernel N={N}: max errors {err}")
+    assert err["pose"] < 1e-6 and err["th"] < 2e-5
+    assert err["rew"] < 1e-5 and err["obs"] < 1e-5
+
+
+# Crowded arena: with a weak wall barrier and strong noise about 5% of the QPs keep five or more
+# active rows (up to seven); h_flag = 10 m^2 flags every QP with an active pair row for the
+# binary64 re-solve.
+CROWDED = dict(xmin=-0.6, xmax=0.6, ymin=-0.5, ymax=0.5, kappa=0.05, noise_amp=0.3)
+WARP_CASES = dict(binary64=dict(h_flag=10.0), crowded=CROWDED,
+                  crowded_binary64=dict(CROWDED, h_flag=10.0),
+                  # 4 envs per warp with a grid stride: the teams' own shared-memory solvers
+                  crowded_binary64_team=dict(CROWDED, h_flag=10.0, warp_envs=4))
+
+
+@pytest.mark.parametrize("case", list(WARP_CASES))
+def test_teacher_forced_warp_rare_qps(rl, case):
+    """2048 envs spread over one block of 4 warps per SM put 3-4 envs in each warp of the shuffle
+    kernel, which then solves its rare QPs -- an active set beyond the four rows of the register
+    solver, and the binary64 re-solve of a flagged QP -- with the whole warp.  Poses,
+    observations and rewards against the oracle stepped from the same state."""
+    g, o = make_pair(0, 4, episode_len=30, small_variant=1, **WARP_CASES[case])
+    err, flagged = _teacher_forced(rl, g, o, [4] * 2048, 57, 30, traces=False)
+    print(f"\nwarp-solved rare QPs, {case}: max errors {err}  binary64 re-solves {flagged}")
+    if "binary64" in case:
+        assert flagged > 1000
     assert err["pose"] < 1e-6 and err["th"] < 2e-5
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
