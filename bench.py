@@ -371,7 +371,9 @@ def run_rollout(a):
     stream.synchronize()
     tuning = None
     if not a.no_tune and w["precision"] == 32:
-        tuning = env.tune(min(100, T))
+        # probes of up to 1000 steps: the slow tail of a rollout (a few envs whose robots stay
+        # jammed for many steps) decides its time and does not show in short probes
+        tuning = env.tune(min(1000, T))
     n_warm = max(3, a.warmup)
     for _ in range(n_warm):
         env.rollout(T, obs, rew, done)

@@ -723,11 +723,12 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
             }
             need = __ballot_sync(wm, i == 0 && k.resolve_f64 && res.flag);
             if (need) {
-                // binary64: projected points from the binary32 pose, as the team re-solve
-                double sd, cd;
-                sincos((double)th, &sd, &cd);
-                const double pxd = (double)x + (double)k.l * cd;
-                const double pyd = (double)y + (double)k.l * sd;
+                // binary64: projected points from the binary32 pose (the heading's sine and
+                // cosine to binary32 accuracy, a few 1e-9 m at the look-ahead distance)
+                float sf, cf;
+                sincosf(th, &sf, &cf);
+                const double pxd = (double)x + (double)k.l * (double)cf;
+                const double pyd = (double)y + (double)k.l * (double)sf;
                 QPConsts<double> dc;
                 dc.gamma = (double)k.gamma; dc.r2 = (double)k.r2; dc.kg = (double)k.kg;
                 dc.half_r = (double)k.half_r; dc.xmin = (double)k.xmin; dc.xmax = (double)k.xmax;

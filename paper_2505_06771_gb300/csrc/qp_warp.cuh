@@ -12,9 +12,10 @@
 // over the active rows' lanes; the short sequential parts (triangular solves on at most 8 rows)
 // run in every lane.  The iteration is the one of thread_qp / qp_solve (Goldfarb-Idnani dual
 // active set on H = I, Sec. 3 barrier QP): add the most violated inactive row (ties: lowest
-// slot), step by min(tf, td), drop a row whose multiplier reaches zero.  In binary64 the final
-// active set is polished as qp_solve does (exact solve of G lam = N u0 - b, kept if it stays
-// feasible).
+// slot), step by min(tf, td), drop a row whose multiplier reaches zero.  Its result is
+// rounded to binary32 by the caller, so the binary64 iterate is not polished by an exact solve
+// on the final active set as the binary64 kernels' qp_solve does (the two differ by binary64
+// rounding).
 #pragma once
 #include "qp_regs.cuh"
 
@@ -33,6 +34,31 @@ __device__ __forceinline__ Q wsel8(const Q (&a)[8], int k) {
     for (int m = 1; m < 8; ++m)
         if (k == m) r = a[m];
     return r;
+}
+
+// Reciprocal, quotient and square root for the dual step.  binary32: the IEEE operations.
+// binary64: a binary32 estimate refined by Newton's method (one step for the reciprocal,
+// r <- r + r (1 - b r); Heron's step s <- s + (x - s^2) / (2 s) for the root), about 2^-46
+// relative, in 2 or 3 binary64 instructions instead of the 10 or more of the IEEE sequences;
+// operands outside the binary32 normal range take the IEEE operation.
+__device__ __forceinline__ float wrcp(float b) { return 1.f / b; }
+__device__ __forceinline__ float wdiv(float a, float b) { return a / b; }
+__device__ __forceinline__ float wsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ bool wnormal(double b) {
+    const double m = fabs(b);
+    return m > 1e-30 && m < 1e30;
+}
+__device__ __forceinline__ double wrcp(double b) {
+    if (!wnormal(b)) return 1.0 / b;
+    const double r = (double)(1.f / (float)b);
+    return fma(r, fma(-b, r, 1.0), r);
+}
+__device__ __forceinline__ double wdiv(double a, double b) { return a * wrcp(b); }
+__device__ __forceinline__ double wsqrt(double x) {
+    if (!wnormal(x) || x < 0.0) return sqrt(x);
+    const float sf = sqrtf((float)x);
+    const double s = (double)sf;
+    return fma(fma(-s, s, x), (double)(0.5f / sf), s);
 }
 
 // Orderable bits of a value >= 0 (0 for "none").
@@ -71,35 +97,33 @@ __device__ __forceinline__ Q warp_sum8(unsigned wm, Q v) {
 }
 
 // Slot s of the QP: pair rows 0..5 as (a, b) with coefficient (cx, cy) on u_a and (-cx, -cy)
-// on u_b; arena rows 6 + 4 i + t with b = -1.
+// on u_b; arena rows 6 + 4 i + t with b = -1.  Branch-free, so that the lanes holding pair rows
+// and those holding arena rows run one instruction stream: a pair row's h = dx^2 + dy^2 - r^2
+// and an arena row's wall distance d are both a difference e1 - e2 (less e3 for the arena),
+// then the bound is gamma h^3 or kappa gamma d^3.
 template <typename Q>
 __device__ __forceinline__ void warp_row(int s, int N, const Q (&Px)[4], const Q (&Py)[4],
                                          const QPConsts<Q>& c, int& a, int& b, Q& cx, Q& cy,
-                                         Q& bv, Q& h, bool& ok) {
-    if (s < 6) {
-        a = slot_a(s);
-        b = slot_b(s);
-        const Q dx = wsel4(Px, a) - wsel4(Px, b), dy = wsel4(Py, a) - wsel4(Py, b);
-        cx = (Q)-2 * dx;
-        cy = (Q)-2 * dy;
-        h = dx * dx + dy * dy - c.r2;
-        bv = c.gamma * h * h * h;
-        ok = b < N;
-    } else {
-        const int m = s - 6, i = m >> 2, t = m & 3;
-        const Q px = wsel4(Px, i), py = wsel4(Py, i);
-        const Q d = (t == 0) ? c.xmax - c.half_r - px
-                  : (t == 1) ? px - c.xmin - c.half_r
-                  : (t == 2) ? c.ymax - c.half_r - py
-                             : py - c.ymin - c.half_r;
-        a = i;
-        b = -1;
-        cx = (t == 0) ? (Q)1 : ((t == 1) ? (Q)-1 : (Q)0);
-        cy = (t == 2) ? (Q)1 : ((t == 3) ? (Q)-1 : (Q)0);
-        bv = c.kg * d * d * d;
-        h = (Q)1e30;
-        ok = (s < 22) && (i < N);
-    }
+                                         Q& bv, bool& ok) {
+    const bool pr = s < 6;
+    const int m = pr ? 0 : s - 6, i = m >> 2, t = m & 3;
+    a = pr ? slot_a(s) : i;
+    b = pr ? slot_b(s) : -1;
+    const Q pax = wsel4(Px, a), pay = wsel4(Py, a);
+    const Q pbx = wsel4(Px, pr ? b : 0), pby = wsel4(Py, pr ? b : 0);
+    const Q own = (t < 2) ? pax : pay;
+    // pair: e1 - e2 = dx; arena t = 0: (xmax - half_r) - px, 1: (px - xmin) - half_r,
+    // 2: (ymax - half_r) - py, 3: (py - ymin) - half_r
+    const Q e1 = pr ? pax : ((t & 1) ? own : (t == 0 ? c.xmax : c.ymax));
+    const Q e2 = pr ? pbx : ((t & 1) ? (t == 1 ? c.xmin : c.ymin) : c.half_r);
+    const Q e3 = (t & 1) ? c.half_r : own;
+    const Q d1 = e1 - e2;
+    const Q dy = pay - pby;
+    const Q val = pr ? d1 * d1 + dy * dy - c.r2 : d1 - e3;
+    bv = (pr ? c.gamma : c.kg) * val * val * val;
+    cx = pr ? (Q)-2 * d1 : ((t == 0) ? (Q)1 : ((t == 1) ? (Q)-1 : (Q)0));
+    cy = pr ? (Q)-2 * dy : ((t == 2) ? (Q)1 : ((t == 3) ? (Q)-1 : (Q)0));
+    ok = s < 22 && (pr ? b < N : i < N);
 }
 
 // Coefficient of a row on unknown m = 2 i + d.
@@ -124,16 +148,21 @@ __device__ __noinline__ QPResult warp_qp(unsigned wm, int nl, int N, const Q (&P
     res.q = 0;
     res.iters = 0;
     res.flag = false;
-    // the lane's row slots s = l + k nl (k < 3 since nl >= 8)
+    // the lane's row slots s = l + k nl, k < K <= 3 (nl >= 8)
+    const int K = (22 + nl - 1) / nl;
     int ra[3], rb[3];
     Q rcx[3], rcy[3], rbv[3], rthr[3];
     bool rok[3];
     unsigned myact = 0u;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+        ra[k] = 0;
+        rb[k] = -1;
+        rcx[k] = rcy[k] = rbv[k] = rthr[k] = (Q)0;
+        rok[k] = false;
+        if (k >= K) continue;
         const int s = l + k * nl;
-        Q hh;
-        warp_row<Q>(s < 22 ? s : 21, N, Px, Py, c, ra[k], rb[k], rcx[k], rcy[k], rbv[k], hh,
+        warp_row<Q>(s < 22 ? s : 21, N, Px, Py, c, ra[k], rb[k], rcx[k], rcy[k], rbv[k],
                     rok[k]);
         rok[k] = rok[k] && s < 22 && l < nl;
         rthr[k] = c.tol_abs + c.tol_rel * fabs(rbv[k]);
@@ -147,6 +176,7 @@ __device__ __noinline__ QPResult warp_qp(unsigned wm, int nl, int N, const Q (&P
         Q bv_own = (Q)0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
+            if (k >= K) continue;
             const int bs = rb[k] >= 0 ? rb[k] : 0;
             const Q uax = __shfl_sync(wm, um, 2 * ra[k]);
             const Q uay = __shfl_sync(wm, um, 2 * ra[k] + 1);
@@ -212,7 +242,7 @@ __device__ __noinline__ QPResult warp_qp(unsigned wm, int nl, int N, const Q (&P
             // dual step bound: min lam_t / r_t over r_t > 0 (lane t), ties to the lowest t
             Q tl = INF;
             if (l < q && r[l] > (Q)0) {
-                tl = lam[l] / r[l];
+                tl = wdiv(lam[l], r[l]);
                 if (tl < (Q)0) tl = (Q)0;
             }
             const int jb = warp_argmin_key(wm, l < q ? wkey(tl) : ~0ull, l);
@@ -225,7 +255,7 @@ __device__ __noinline__ QPResult warp_qp(unsigned wm, int nl, int N, const Q (&P
                                    : pcx * uax + pcy * uay - pbv;
             const bool indep = zz > c.eps_dep * app;
             if (!indep) res.flag = true;
-            const Q tf = indep ? sp / zz : INF;
+            const Q tf = indep ? wdiv(sp, zz) : INF;
             if (!(tf < INF) && !(td < INF)) {
                 res.status = 1;
                 break;
@@ -236,10 +266,10 @@ __device__ __noinline__ QPResult warp_qp(unsigned wm, int nl, int N, const Q (&P
             lam_p += st;
             if (tf <= td) {
                 if (q == kWarpRows) { res.status = 2; break; }
-                const Q dg = sqrt(zz);
+                const Q dg = wsqrt(zz);
                 for (int m = 0; m < q; ++m) L[q * (q + 1) / 2 + m] = y[m];
                 L[q * (q + 1) / 2 + q] = dg;
-                dinv[q] = (Q)1 / dg;
+                dinv[q] = wrcp(dg);
                 As[q] = sp_slot;
                 Aa[q] = pa;
                 Ab[q] = pb;
@@ -287,45 +317,6 @@ __device__ __noinline__ QPResult warp_qp(unsigned wm, int nl, int N, const Q (&P
         sp_slot = scan(vb);
     }
     res.q = q;
-    if (std::is_same<Q, double>::value && res.status == 0 && q > 0) {
-        // exact solve on the final active set, G lam = N u0 - b, u = u0 - N^T lam; kept when
-        // every multiplier is >= -tol_lam and the point stays feasible
-        Q wl = (Q)0;
-        if (l < q) {
-            const int a = Aa[l], b = Ab[l];
-            const Q u0ax = wsel8(U0, 2 * a), u0ay = wsel8(U0, 2 * a + 1);
-            const Q u0bx = b >= 0 ? wsel8(U0, 2 * b) : (Q)0, u0by = b >= 0 ? wsel8(U0, 2 * b + 1) : (Q)0;
-            wl = (b >= 0 ? Acx[l] * (u0ax - u0bx) + Acy[l] * (u0ay - u0by)
-                         : Acx[l] * u0ax + Acy[l] * u0ay) - Abv[l];
-        }
-        Q y[kWarpRows], lz[kWarpRows];
-        for (int t = 0; t < q; ++t) {
-            Q s = __shfl_sync(wm, wl, t);
-            for (int m = 0; m < t; ++m) s -= L[t * (t + 1) / 2 + m] * y[m];
-            y[t] = s * dinv[t];
-        }
-        bool dual_ok = true;
-        for (int t = q - 1; t >= 0; --t) {
-            Q s = y[t];
-            for (int m = t + 1; m < q; ++m) s -= L[m * (m + 1) / 2 + t] * lz[m];
-            lz[t] = s * dinv[t];
-            if (lz[t] < -c.tol_lam) dual_ok = false;
-        }
-        if (dual_ok) {
-            const Q keep = um;
-            if (l < 8) {
-                Q u = wsel8(U0, l);
-                for (int t = 0; t < q; ++t) u -= lz[t] * warp_coef<Q>(Aa[t], Ab[t], Acx[t], Acy[t], l);
-                um = u;
-            }
-            const unsigned act_keep = myact;
-            myact = 0u;
-            Q vpol;
-            const int viol = scan(vpol);
-            myact = act_keep;
-            if (viol >= 0) um = keep;
-        }
-    }
     if (res.status == 0) {
         for (int t = 0; t < q; ++t)
             if (Ab[t] >= 0) {
