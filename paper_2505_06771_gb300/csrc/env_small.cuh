@@ -576,10 +576,11 @@ static __device__ __noinline__ void small_disc_obs(const TeamSmem<float, 4>& S, 
 // scripted nominal control and no traces, every such branch folded away at compile time.
 // SCEN >= 0 fixes the scenario at compile time and LEAN drops policy actions and traces (the
 // one-launch kernel's scripted rollouts).
-// wm (scripted Navigation only): the lanes of the warp's live teams, all running the same steps
-// in step with each other, when there are at least two; the rare QPs (an active set beyond the
+// wm (scripted Navigation): the lanes of the warp's live teams, all running the same steps in
+// step with each other, when there are at least two; the rare QPs (an active set beyond the
 // register solver's, the binary64 re-solve) are then solved by the whole warp (qp_warp.cuh).
-// 0: each team solves its own in shared memory.
+// 0: each team solves its own in shared memory.  (The general kernel keeps the team solvers:
+// measured on GB300, the warp path's code slowed its common path by about 2%.)
 template <bool FAST, int SCEN = -1, bool LEAN = false>
 __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
                               TeamSmem<float, 4>& S, int e, unsigned wm = 0u) {

@@ -196,23 +196,33 @@ def test_teacher_forced_fast_kernels(rl, kern, N, E):
 # active rows (up to seven); h_flag = 10 m^2 flags every QP with an active pair row for the
 # binary64 re-solve.
 CROWDED = dict(xmin=-0.6, xmax=0.6, ymin=-0.5, ymax=0.5, kappa=0.05, noise_amp=0.3)
-WARP_CASES = dict(binary64=dict(h_flag=10.0), crowded=CROWDED,
-                  crowded_binary64=dict(CROWDED, h_flag=10.0),
+WARP_CASES = dict(binary64=(0, dict(h_flag=10.0), False),
+                  crowded=(0, CROWDED, False),
+                  crowded_binary64=(0, dict(CROWDED, h_flag=10.0), False),
                   # 4 envs per warp with a grid stride: the teams' own shared-memory solvers
-                  crowded_binary64_team=dict(CROWDED, h_flag=10.0, warp_envs=4))
+                  crowded_binary64_team=(0, dict(CROWDED, h_flag=10.0, warp_envs=4), False),
+                  # with traces: the general 4-robot kernel and its team solvers, filtered
+                  # controls compared too
+                  crowded_binary64_traces=(0, dict(CROWDED, h_flag=10.0), True),
+                  discovery_binary64=(2, dict(CROWDED, h_flag=10.0), True))
 
 
 @pytest.mark.parametrize("case", list(WARP_CASES))
 def test_teacher_forced_warp_rare_qps(rl, case):
     """2048 envs spread over one block of 4 warps per SM put 3-4 envs in each warp of the shuffle
     kernel, which then solves its rare QPs -- an active set beyond the four rows of the register
-    solver, and the binary64 re-solve of a flagged QP -- with the whole warp.  Poses,
-    observations and rewards against the oracle stepped from the same state."""
-    g, o = make_pair(0, 4, episode_len=30, small_variant=1, **WARP_CASES[case])
-    err, flagged = _teacher_forced(rl, g, o, [4] * 2048, 57, 30, traces=False)
+    solver, and the binary64 re-solve of a flagged QP -- with the whole warp; the same crowded
+    batches through the teams' own solvers as controls.  Poses, observations and rewards (and
+    with traces the filtered controls) against the oracle stepped from the same state."""
+    scen, kw, traces = WARP_CASES[case]
+    extra = {} if traces else dict(small_variant=1)
+    g, o = make_pair(scen, 4, episode_len=30, **extra, **kw)
+    err, flagged = _teacher_forced(rl, g, o, [4] * 2048, 57, 30, traces=traces)
     print(f"\nwarp-solved rare QPs, {case}: max errors {err}  binary64 re-solves {flagged}")
     if "binary64" in case:
         assert flagged > 1000
+    if traces:
+        assert err["u_star"] < U_TOL
     assert err["pose"] < 1e-6 and err["th"] < 2e-5
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
