@@ -176,8 +176,10 @@ FAST_KERNELS = dict(shuffle=dict(small_variant=1), gather=dict(small_variant=2),
                     thread=dict(lanes=1))
 
 
+# E = 1: the spread launch's single block; E = 5000: more envs than 8 per warp of one block per
+# SM (4864 on 152 SMs), so the team kernels fall back to a grid stride
 @pytest.mark.parametrize("kern", list(FAST_KERNELS))
-@pytest.mark.parametrize("N,E", [(4, 600), (3, 300), (2, 200)])
+@pytest.mark.parametrize("N,E", [(4, 600), (3, 300), (2, 200), (4, 1), (4, 5000)])
 def test_teacher_forced_fast_kernels(rl, kern, N, E):
     """The Navigation fast paths (scripted nominal control, no traces): the 4-lane team kernel
     that reduces with shuffles, the one that publishes robot state in shared memory, and one
