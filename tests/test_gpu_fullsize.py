@@ -1,8 +1,8 @@
 """Parity at the full sizes of the benchmark's workloads, in the launch configuration the
 benchmark times: the GPU batch is first driven into a random state by a scripted rollout, then
 stepped a few times (the step selects the same kernels as the rollout: the 4-robot shuffle team
-kernel with 8 envs per warp for 4096 x 4, the per-class team kernels otherwise), with the FP64
-oracle stepped from the same states over the whole batch."""
+kernel in its spread launch, 6-7 envs per warp, for 4096 x 4; the per-class team kernels
+otherwise), with the FP64 oracle stepped from the same states over the whole batch."""
 import numpy as np
 import pytest
 import torch
