@@ -114,7 +114,8 @@ typedef struct {
     double min_sep;         /* reset: pairwise separation of robot centres [m] (0.3) */
     double near_frac;       /* reset: share of envs with one near pair (0) */
     double near_dmin, near_dmax;     /* reset: distance of the near pair [m] (0.18, 0.20) */
-    double h_flag;          /* flag a binary32 QP with an active pair whose h < h_flag (1e-3) */
+    double h_flag;          /* also re-solve in binary64 a binary32 QP with an active pair whose
+                               h < h_flag (m^2); default -1: never (h >= -r^2) */
     double goal_eps;        /* Navigation: > 0 gives a robot a new goal when its projected point
                                ends a step within goal_eps of its goal (Random Waypoint
                                Navigation, Sec. 4.2); 0 (default) keeps goals for the episode */

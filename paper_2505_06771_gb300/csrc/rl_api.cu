@@ -377,7 +377,10 @@ rl_status rl_config_default(int32_t scenario, rl_config* out) {
     out->near_frac = 0.0;
     out->near_dmin = 0.18;
     out->near_dmax = 0.20;
-    out->h_flag = 1e-3;
+    // No small-h trigger by default (h >= -r^2 > -1): on 278 active QPs with h < 1e-3 m^2 met in
+    // 16.4 M oracle env-steps, a binary32 solve was as close to the binary64 minimiser (6.9e-8)
+    // as on the others (tests/test_binary32_small_h.py)
+    out->h_flag = -1.0;
     out->goal_eps = 0.0;
     out->controller = RL_CTRL_POSITION;
     out->pose_k1 = 1.0;

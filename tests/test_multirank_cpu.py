@@ -31,7 +31,8 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_max_time_and_job_rate():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    # the manager process is spawned too: forking this (multi-threaded) process could deadlock
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
