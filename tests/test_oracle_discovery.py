@@ -1,4 +1,4 @@
-"""Pins of the oracle's Discovery scenario (SURVEY f4; App. B "Discovery": sensing robots sense
+"""Pins of the oracle's Discovery scenario (App. B "Discovery": sensing robots sense
 landmarks within their sensing radius, tagging robots tag landmarks within their tagging
 radius, rewards 1 per landmark sensed and 5 per landmark tagged, a 0.05 penalty per step while
 a landmark is left to tag, no collision penalty; 4 robots, 2 of each role, radii 0.45 and

@@ -1,4 +1,4 @@
-"""Pins of the oracle's unicycle pose controller (SURVEY f3; the paper's Sec. 4.2 evaluates a pose
+"""Pins of the oracle's unicycle pose controller (the paper's Sec. 4.2 evaluates a pose
 controller without giving its law, so the published posture-regulation law of Aicardi et al.
 (1995) stands for it) and of its plumbing into the Navigation step (CPU only).
 
