@@ -142,6 +142,8 @@ typedef struct {
 rl_status rl_config_default(int32_t scenario, rl_config* out);
 
 /* Create a batch of n_envs environments and reset them (episode 0) with seed.
+   Passage: Sec. 6.1 (RobotariumEnv holds a batch of robots; a Scenario defines their reset,
+   step, reward and observation) and App. B (the scenarios' initial distributions).
    h_n_robots: host array [n_envs] of robot counts in [1, 32], or NULL to give every env
    n_robots_uniform robots.  stream: a cudaStream_t; NULL makes the handle create its own
    stream, which is ordered with the legacy default stream.
@@ -150,7 +152,8 @@ rl_status rl_config_default(int32_t scenario, rl_config* out);
 rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_robots,
                     int32_t n_robots_uniform, uint64_t seed, void* stream, rl_env** out);
 
-/* Reset every env to episode 0 under a new seed and zero the counters. */
+/* Reset every env to episode 0 under a new seed and zero the counters.
+   Passage: Sec. 6.1 (Scenario reset: robots and goals drawn anew for each episode). */
 rl_status rl_reset(rl_env* env, uint64_t seed);
 
 /* One step of every env (Dec-POMDP step: joint action -> per-agent observations, team reward,
@@ -165,7 +168,8 @@ rl_status rl_step(rl_env* env, const void* d_actions, void* d_obs, void* d_rewar
 rl_status rl_step_io_call(rl_env* env, const rl_step_io* io);
 
 /* T scripted steps of every env in one persistent launch (replayed from a CUDA graph), the
-   state kept on chip across steps.  d_obs_traj [T][rows][obs_dim], d_rew_traj [T][E],
+   state kept on chip across steps.  Passage: Sec. 4.1 (the step jit-compiled and vmapped over
+   environments, whole rollouts run on the accelerator); here that batching is one launch.  d_obs_traj [T][rows][obs_dim], d_rew_traj [T][E],
    d_done_traj [T][E]; any may be NULL.  RL_ERR_STATE if the handle is not scripted. */
 rl_status rl_rollout(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew_traj,
                      uint8_t* d_done_traj);
@@ -185,9 +189,17 @@ rl_status rl_rollout_plain(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew
    Synchronises the stream.  RL_ERR_STATE if the handle is not scripted. */
 rl_status rl_tune(rl_env* env, int32_t T_probe, int32_t* h_choice);
 
+/* Uneven binary32 batches (more than one robot-count class): on = 1 runs rl_rollout as one
+   persistent launch over every class (the default, and rl_tune's candidate), on = 0 as one
+   launch per class.  Same results either way up to rounding.  RL_ERR_STATE for a batch with one
+   class or a binary64 handle, RL_ERR_ARG for other values of on. */
+rl_status rl_set_one_launch(rl_env* env, int32_t on);
+
 /* End to end through host memory: upload h_state (rl_state_bytes() bytes, or NULL to keep the
-   device state), run rl_rollout, and copy the trajectories to the host buffers (pinned memory
-   recommended; any may be NULL).  Returns after the copies completed. */
+   device state), run the T steps, and copy the trajectories to the host buffers (pinned memory
+   recommended; any may be NULL).  The steps run in up to 8 chunks, one launch each; each
+   chunk's slice of the trajectories is downloaded on a second stream while the next chunk
+   runs.  Same results as rl_rollout.  Returns after the copies completed. */
 rl_status rl_rollout_host(rl_env* env, const void* h_state, int32_t T, void* h_obs_traj,
                           void* h_rew_traj, uint8_t* h_done_traj);
 
@@ -286,7 +298,7 @@ rl_status rl_server_destroy(rl_server* srv);
    Binary32 handles with policy actions (scripted = 0) only. */
 typedef struct rl_policy rl_policy;
 
-/* hidden: H, a multiple of 32 up to 512.  Host arrays, row-major: h_w1 [H][obs_dim], h_b1 [H],
+/* Passage: App. A (policy architecture).  hidden: H, a multiple of 32 up to 512.  Host arrays, row-major: h_w1 [H][obs_dim], h_b1 [H],
    h_wi [3H][H], h_bi [3H], h_wh [3H][H], h_bh [3H] (gate blocks in the order r, z, n),
    h_wo [2][H], h_bo [2].  Copies the weights to the device; the recurrent state starts at 0. */
 rl_status rl_policy_create(rl_env* env, int32_t hidden, const float* h_w1, const float* h_b1,
@@ -309,9 +321,9 @@ void      rl_policy_destroy(rl_policy* pol);   /* NULL-safe; waits for the handl
    handles; RL_ERR_ARG otherwise). */
 rl_status rl_observe(rl_env* env, void* d_obs);
 
-int32_t     rl_obs_dim(const rl_env* env);
-int32_t     rl_n_envs(const rl_env* env);
-int32_t     rl_total_robots(const rl_env* env);
+int32_t     rl_obs_dim(const rl_env* env);      /* values per robot observation row */
+int32_t     rl_n_envs(const rl_env* env);       /* environments E */
+int32_t     rl_total_robots(const rl_env* env); /* robot rows, the sum of n_e */
 int32_t     rl_lanes(const rl_env* env);        /* lanes per env the handle runs with */
 const char* rl_last_error(const rl_env* env);   /* never NULL */
 void        rl_destroy(rl_env* env);            /* NULL-safe; waits for the stream */

@@ -20,7 +20,8 @@ from .build import LIB as LIB_PATH
 from .build import build
 
 __all__ = ["build", "lib", "config_default", "Env", "Server", "Policy", "RLError", "NAVIGATION",
-           "FORAGING", "DISCOVERY", "COUNTERS", "exported_symbols", "rollout_noalloc", "noalloc_state_bytes"]
+           "FORAGING", "DISCOVERY", "COUNTERS", "exported_symbols", "rollout_noalloc", "noalloc_state_bytes",
+           "noalloc_max_bytes"]
 
 NAVIGATION, FORAGING, DISCOVERY = 0, 1, 2
 COUNTERS = ("collisions", "oob", "success", "qp_active", "qp_flagged", "qp_infeasible",
@@ -115,6 +116,7 @@ def lib():
         L.rl_destroy.argtypes = [vp]
         L.rl_destroy.restype = None
         L.rl_tune.argtypes = [vp, i32, vp]
+        L.rl_set_one_launch.argtypes = [vp, i32]
         L.rl_server_create.argtypes = [ctypes.POINTER(RLConfig), sz, i32, ctypes.POINTER(vp)]
         L.rl_server_submit.argtypes = [vp, ctypes.POINTER(RLRequest),
                                        ctypes.POINTER(ctypes.c_uint64)]
@@ -274,6 +276,10 @@ class Env:
                                  block_threads=int(out[3 + 5 * c]),
                                  warp_envs=int(out[4 + 5 * c]), variant=int(out[5 + 5 * c]))
                             for c in range(5) if out[1 + 5 * c] > 0]}
+
+    def set_one_launch(self, on: bool):
+        """rl_set_one_launch: uneven batches as one persistent launch (True) or one per class."""
+        self._check(self._L.rl_set_one_launch(self._h, 1 if on else 0), "rl_set_one_launch")
 
     def state_bytes(self) -> int:
         return int(self._L.rl_state_bytes(self._h))
@@ -457,6 +463,15 @@ class Server:
 
 def noalloc_state_bytes(cfg: dict, n_envs: int, n_robots: int) -> int:
     return int(lib().rl_noalloc_state_bytes(ctypes.byref(_to_struct(cfg)), n_envs, n_robots))
+
+
+def noalloc_max_bytes() -> int:
+    """RL_NOALLOC_MAX_BYTES as include/rl.h defines it: the state a no-allocation rollout holds."""
+    m = re.search(r"#define\s+RL_NOALLOC_MAX_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)",
+                  open(_HDR).read())
+    if not m:
+        raise RuntimeError("RL_NOALLOC_MAX_BYTES not found in include/rl.h")
+    return int(m.group(1)) << int(m.group(2))
 
 
 _SEGS = [("x", "r", "T"), ("y", "r", "T"), ("th", "r", "T"), ("gx", "r", "T"), ("gy", "r", "T"),

@@ -23,6 +23,7 @@ namespace {
 constexpr uint32_t kMagic = 0x31534C52u;  // "RLS1"
 constexpr uint32_t kVersion = 2u;
 constexpr int kSegs = 17;
+constexpr int kHostChunks = 8;  // rl_rollout_host: chunks of the rollout, one launch each
 enum Seg { S_X = 0, S_Y, S_TH, S_GX, S_GY, S_LEVEL, S_T, S_EP, S_NRES, S_QX, S_QY, S_QLEVEL,
            S_QACTIVE, S_COUNTERS, S_NROB, S_OFF, S_GTH };
 
@@ -62,9 +63,11 @@ struct rl_env {
     int g_T = -1;
     void *g_obs = nullptr, *g_rew = nullptr;
     uint8_t* g_done = nullptr;
-    // device scratch of rl_rollout_host
+    // device scratch of rl_rollout_host, its copy stream and chunk events
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t chunk_ev[kHostChunks] = {};
     // one persistent launch over all classes (binary32, uneven batches)
     int use_multi = 0;
     int n_items = 0;
@@ -80,6 +83,38 @@ cudaStream_t env_stream(const rl_env* h) { return h->st; }
 const std::vector<int32_t>& env_offsets(const rl_env* h) { return h->h_off; }
 const rl_config& env_config(const rl_env* h) { return h->cfg; }
 void env_set_error(rl_env* h, const std::string& msg) { h->err = msg; }
+
+bool valid_config(const rl_config& c, std::string& why) {
+    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING &&
+        c.scenario != RL_SCEN_DISCOVERY) { why = "scenario"; return false; }
+    if (c.precision != RL_PREC_F32 && c.precision != RL_PREC_F64) { why = "precision"; return false; }
+    if (c.episode_len < 1) { why = "episode_len"; return false; }
+    if (c.max_attempts < 1) { why = "max_attempts"; return false; }
+    if (!(c.l > 0) || !(c.vmax > 0) || !(c.wmax > 0) || !(c.dt > 0) || !(c.r >= 0)) { why = "constants"; return false; }
+    if (!(c.xmax > c.xmin) || !(c.ymax > c.ymin)) { why = "arena"; return false; }
+    if (c.scenario != RL_SCEN_NAVIGATION) {
+        if (c.r_max < 1 || c.r_max > kMaxRes) { why = "r_max"; return false; }
+        if (c.n_res_min < 0 || c.n_res_max > c.r_max || c.n_res_min > c.n_res_max) { why = "n_res"; return false; }
+    }
+    if (c.n_max < 0 || c.n_max > kMaxRobots) { why = "n_max"; return false; }
+    if (c.block_threads < 0 || c.block_threads % 32 != 0 || c.block_threads > 256) {
+        why = "block_threads";
+        return false;
+    }
+    if (c.lanes < 0 || c.warp_envs < 0) { why = "lanes / warp_envs"; return false; }
+    if (!(c.goal_eps >= 0.0) || (c.goal_eps > 0.0 && c.scenario != RL_SCEN_NAVIGATION)) {
+        why = "goal_eps";
+        return false;
+    }
+    if ((c.controller != RL_CTRL_POSITION && c.controller != RL_CTRL_POSE) ||
+        (c.controller == RL_CTRL_POSE &&
+         (c.scenario != RL_SCEN_NAVIGATION || !(c.pose_k1 > 0) || !(c.pose_k2 > 0) ||
+          !(c.pose_k3 > 0)))) {
+        why = "controller";
+        return false;
+    }
+    return true;
+}
 }  // namespace rl
 
 namespace {
@@ -104,33 +139,6 @@ rl_status fail(rl_env* h, rl_status s, const std::string& msg) {
 
 rl_status cuda_fail(rl_env* h, cudaError_t e, const char* where) {
     return fail(h, RL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-bool valid_cfg(const rl_config& c, std::string& why) {
-    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING &&
-        c.scenario != RL_SCEN_DISCOVERY) { why = "scenario"; return false; }
-    if (c.precision != RL_PREC_F32 && c.precision != RL_PREC_F64) { why = "precision"; return false; }
-    if (c.episode_len < 1) { why = "episode_len"; return false; }
-    if (c.max_attempts < 1) { why = "max_attempts"; return false; }
-    if (!(c.l > 0) || !(c.vmax > 0) || !(c.wmax > 0) || !(c.dt > 0) || !(c.r >= 0)) { why = "constants"; return false; }
-    if (!(c.xmax > c.xmin) || !(c.ymax > c.ymin)) { why = "arena"; return false; }
-    if (c.scenario != RL_SCEN_NAVIGATION) {
-        if (c.r_max < 1 || c.r_max > rl::kMaxRes) { why = "r_max"; return false; }
-        if (c.n_res_min < 0 || c.n_res_max > c.r_max || c.n_res_min > c.n_res_max) { why = "n_res"; return false; }
-    }
-    if (c.n_max < 0 || c.n_max > rl::kMaxRobots) { why = "n_max"; return false; }
-    if (!(c.goal_eps >= 0.0) || (c.goal_eps > 0.0 && c.scenario != RL_SCEN_NAVIGATION)) {
-        why = "goal_eps";
-        return false;
-    }
-    if ((c.controller != RL_CTRL_POSITION && c.controller != RL_CTRL_POSE) ||
-        (c.controller == RL_CTRL_POSE &&
-         (c.scenario != RL_SCEN_NAVIGATION || !(c.pose_k1 > 0) || !(c.pose_k2 > 0) ||
-          !(c.pose_k3 > 0)))) {
-        why = "controller";
-        return false;
-    }
-    return true;
 }
 
 template <typename R>
@@ -399,7 +407,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
     if (!cfg || !out || n_envs < 1) return RL_ERR_ARG;
     *out = nullptr;
     std::string why;
-    if (!valid_cfg(*cfg, why)) return RL_ERR_ARG;
+    if (!rl::valid_config(*cfg, why)) return RL_ERR_ARG;
     rl_env* h = new (std::nothrow) rl_env();
     if (!h) return RL_ERR_OOM;
     h->cfg = *cfg;
@@ -742,6 +750,15 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     return RL_OK;
 }
 
+rl_status rl_set_one_launch(rl_env* h, int32_t on) {
+    if (!h || (on != 0 && on != 1)) return RL_ERR_ARG;
+    if (h->n_items == 0)
+        return fail(h, RL_ERR_STATE, "rl_set_one_launch: the batch has one size class (or is binary64)");
+    if (h->use_multi != on) drop_graph(h);
+    h->use_multi = on;
+    return RL_OK;
+}
+
 size_t rl_state_bytes(const rl_env* h) { return h ? sizeof(StateHeader) + h->img_bytes : 0; }
 
 rl_status rl_get_state(rl_env* h, void* dst, size_t bytes) {
@@ -815,12 +832,40 @@ rl_status rl_rollout_host(rl_env* h, const void* h_state, int32_t T, void* h_obs
     void* d_obs = h_obs ? base : nullptr;
     void* d_rew = h_rew ? base + ((ob + 255) & ~(size_t)255) : nullptr;
     uint8_t* d_done = h_done ? (uint8_t*)(base + ((ob + 255) & ~(size_t)255) + ((rb + 255) & ~(size_t)255)) : nullptr;
-    rl_status s = rl_rollout(h, T, d_obs, d_rew, d_done);
-    if (s != RL_OK) return s;
+    if (T == 0) return RL_OK;
+    // The rollout in chunks of steps, each chunk one launch on the handle's stream; after a
+    // chunk's launch an event, on which the copy stream waits before downloading that chunk's
+    // slice of the trajectories.  Chunk k's download overlaps chunk k + 1's compute, so the call
+    // takes about max(compute, copy) instead of their sum.  Chunking gives the same results:
+    // the kernels write the state back after a chunk and read it at the next.
     cudaError_t e = cudaSuccess;
-    if (h_obs) e = cudaMemcpyAsync(h_obs, d_obs, ob, cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess && h_rew) e = cudaMemcpyAsync(h_rew, d_rew, rb, cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess && h_done) e = cudaMemcpyAsync(h_done, d_done, db, cudaMemcpyDeviceToHost, h->st);
+    if (!h->copy_st) {
+        e = cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking);
+        for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&h->chunk_ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "rollout_host streams");
+    }
+    const int nck = std::min(kHostChunks, (int)T);
+    const size_t ostep = (size_t)h->total * h->obs_dim * h->esz, rstep = (size_t)h->E * h->esz;
+    for (int k = 0; k < nck && e == cudaSuccess; ++k) {
+        const size_t t0 = (size_t)T * k / nck, t1 = (size_t)T * (k + 1) / nck;
+        rl_status s = rollout_enqueue(h, (int)(t1 - t0), d_obs ? (char*)d_obs + t0 * ostep : nullptr,
+                                      d_rew ? (char*)d_rew + t0 * rstep : nullptr,
+                                      d_done ? d_done + t0 * h->E : nullptr);
+        if (s != RL_OK) return s;
+        e = cudaEventRecord(h->chunk_ev[k], h->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_st, h->chunk_ev[k], 0);
+        if (e == cudaSuccess && h_obs)
+            e = cudaMemcpyAsync((char*)h_obs + t0 * ostep, (char*)d_obs + t0 * ostep,
+                                (t1 - t0) * ostep, cudaMemcpyDeviceToHost, h->copy_st);
+        if (e == cudaSuccess && h_rew)
+            e = cudaMemcpyAsync((char*)h_rew + t0 * rstep, (char*)d_rew + t0 * rstep,
+                                (t1 - t0) * rstep, cudaMemcpyDeviceToHost, h->copy_st);
+        if (e == cudaSuccess && h_done)
+            e = cudaMemcpyAsync(h_done + t0 * h->E, d_done + t0 * h->E, (t1 - t0) * h->E,
+                                cudaMemcpyDeviceToHost, h->copy_st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "rollout_host download");
     return RL_OK;
@@ -851,6 +896,12 @@ void rl_destroy(rl_env* h) {
     drop_graph(h);
     // stream-ordered frees: no device-wide synchronisation
     if (h->d_scratch) cudaFreeAsync(h->d_scratch, h->st);
+    if (h->copy_st) {
+        cudaStreamSynchronize(h->copy_st);
+        for (int k = 0; k < kHostChunks; ++k)
+            if (h->chunk_ev[k]) cudaEventDestroy(h->chunk_ev[k]);
+        cudaStreamDestroy(h->copy_st);
+    }
     if (h->d_lists) cudaFreeAsync(h->d_lists, h->st);
     if (h->d_items) cudaFreeAsync(h->d_items, h->st);
     if (h->d_img) cudaFreeAsync(h->d_img, h->st);
@@ -1039,7 +1090,7 @@ rl_status rl_server_create(const rl_config* cfg, size_t hbm_budget_bytes, int32_
                            rl_server** out) {
     if (!cfg || !out || max_slots < 1 || hbm_budget_bytes == 0) return RL_ERR_ARG;
     std::string why;
-    if (!valid_cfg(*cfg, why)) return RL_ERR_ARG;
+    if (!rl::valid_config(*cfg, why)) return RL_ERR_ARG;
     rl_server* S = new (std::nothrow) rl_server();
     if (!S) return RL_ERR_OOM;
     S->cfg = *cfg;

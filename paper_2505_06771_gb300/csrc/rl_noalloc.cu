@@ -8,17 +8,21 @@
 // The kernels are the same ones rl_rollout launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "../../include/rl.h"
+#include "internal.h"
 #include "launch.h"
 
 namespace {
 
-constexpr size_t kStaticBytes = size_t(8) << 20;  // RL_NOALLOC_MAX_BYTES
+constexpr size_t kStaticBytes = RL_NOALLOC_MAX_BYTES;
+static_assert(kStaticBytes % 256 == 0, "the static state array holds 256-byte segments");
 static __device__ __align__(256) unsigned char g_noalloc_state[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
@@ -130,11 +134,19 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     a.env_begin = 0;
     a.seed = seed;
 
-    // the robot-count class this batch runs in, with its default lanes and block size
-    int nmax_class = 32, lanes = 32;
-    for (int ci = 0; ci < rl::kNumClasses; ++ci)
-        if (N <= rl::kClassNmax[ci]) { nmax_class = rl::kClassNmax[ci]; lanes = rl::kClassLanes[ci]; break; }
-    const int bt = nmax_class <= 16 ? 64 : 32;
+    // the robot-count class this batch runs in, with the launch shape rl_create would give it
+    // (the configuration's lanes, block size, envs per warp and 4-robot variant, else the
+    // class defaults)
+    int ci = 0;
+    while (ci + 1 < rl::kNumClasses && N > rl::kClassNmax[ci]) ++ci;
+    const int nmax_class = rl::kClassNmax[ci];
+    const unsigned ok = rl::supported_lanes(c.precision, nmax_class);
+    int lanes = c.lanes > 0 ? c.lanes : rl::kClassLanes[ci];
+    if (!(ok & (unsigned)lanes)) lanes = rl::kClassLanes[ci];
+    int bt = nmax_class <= 16 ? 64 : 32;
+    if (c.block_threads > 0) bt = std::max(c.block_threads, lanes);
+    a.warp_envs = c.warp_envs > 0 ? std::min(32, c.warp_envs) : 0;
+    a.variant = (c.small_variant == 1 || c.small_variant == 2) ? c.small_variant : 0;
     auto launch = [&](bool reset) -> cudaError_t {
         if constexpr (std::is_same<R, double>::value) {
             return rl::launch_f64(a, nmax_class, lanes, bt, 0, st, reset);
@@ -177,26 +189,10 @@ extern "C" rl_status rl_rollout_noalloc(const rl_config* cfg, int32_t n_envs, in
                                         void* d_rew_traj, uint8_t* d_done_traj, void* stream) {
     if (!cfg || n_envs < 1 || n_robots < 1 || n_robots > rl::kMaxRobots || T < 0) return RL_ERR_ARG;
     const rl_config& c = *cfg;
-    if (c.scenario != RL_SCEN_NAVIGATION && c.scenario != RL_SCEN_FORAGING &&
-        c.scenario != RL_SCEN_DISCOVERY)
-        return RL_ERR_ARG;
-    if (c.precision != RL_PREC_F32 && c.precision != RL_PREC_F64) return RL_ERR_ARG;
-    if (!c.scripted || c.episode_len < 1 || c.max_attempts < 1) return RL_ERR_ARG;
+    std::string why;
+    if (!rl::valid_config(c, why)) return RL_ERR_ARG;  // the checks rl_create makes
+    if (!c.scripted) return RL_ERR_ARG;
     if (c.n_max != 0 && c.n_max < n_robots) return RL_ERR_ARG;
-    if (c.scenario != RL_SCEN_NAVIGATION &&
-        (c.r_max < 1 || c.r_max > rl::kMaxRes || c.n_res_min < 0 || c.n_res_max > c.r_max ||
-         c.n_res_min > c.n_res_max))
-        return RL_ERR_ARG;
-    if (!(c.l > 0) || !(c.vmax > 0) || !(c.wmax > 0) || !(c.dt > 0) || !(c.xmax > c.xmin) ||
-        !(c.ymax > c.ymin))
-        return RL_ERR_ARG;
-    if (!(c.goal_eps >= 0.0) || (c.goal_eps > 0.0 && c.scenario != RL_SCEN_NAVIGATION))
-        return RL_ERR_ARG;
-    if ((c.controller != RL_CTRL_POSITION && c.controller != RL_CTRL_POSE) ||
-        (c.controller == RL_CTRL_POSE &&
-         (c.scenario != RL_SCEN_NAVIGATION || !(c.pose_k1 > 0) || !(c.pose_k2 > 0) ||
-          !(c.pose_k3 > 0))))
-        return RL_ERR_ARG;
     if (rl_noalloc_state_bytes(cfg, n_envs, n_robots) > kStaticBytes) return RL_ERR_ARG;
     void* base = nullptr;
     if (state_address(&base) != cudaSuccess) return RL_ERR_CUDA;

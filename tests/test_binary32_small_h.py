@@ -119,3 +119,102 @@ def test_binary32_small_h_as_accurate_as_others():
     # the near-contact QPs no worse than the others
     assert eo.max() < 1e-6
     assert es.max() <= max(2 * eo.max(), 1e-7)
+
+
+def solve32_vec(A, b, u0, max_iter=200):
+    """solve32 with the row scan vectorised (A u - b in binary32), for 40-variable QPs."""
+    A = np.asarray(A, F)
+    b = np.asarray(b, F)
+    n, m = len(u0), len(A)
+    u = u0.copy()
+    act, lam = [], []
+    tol_abs, tol_rel, eps_dep = F(2e-7), F(1e-6), F(1e-5)
+    thr = (tol_abs + tol_rel * np.abs(b)).astype(F)
+    for _ in range(max_iter):
+        v = (A @ u).astype(F) - b
+        v[act] = F(0)
+        ok = v > thr
+        if not ok.any():
+            return u, 0
+        kb = int(np.argmax(np.where(ok, v, F(-np.inf))))  # ties: lowest index
+        ap = A[kb]
+        lam_p = F(0)
+        while True:
+            if act:
+                Nm = A[act]
+                G = (Nm @ Nm.T).astype(F)
+                r = np.linalg.solve(G, (Nm @ ap).astype(F)).astype(F)
+                z = (ap - Nm.T @ r).astype(F)
+            else:
+                r, z = np.zeros(0, F), ap.copy()
+            zz = F(np.dot(z, z))
+            td, jb = F(np.inf), -1
+            for t in range(len(act)):
+                if r[t] > 0 and F(lam[t] / r[t]) < td:
+                    td, jb = F(lam[t] / r[t]), t
+            sp = F(np.dot(ap, u)) - b[kb]
+            tf = sp / zz if zz > eps_dep * F(np.dot(ap, ap)) else F(np.inf)
+            if not np.isfinite(tf) and not np.isfinite(td):
+                return np.zeros(n, F), 1
+            st = min(tf, td)
+            if np.isfinite(tf):
+                u = (u - st * z).astype(F)
+            lam = [F(lv - st * r[t]) for t, lv in enumerate(lam)]
+            lam_p = F(lam_p + st)
+            if tf <= td:
+                act.append(kb)
+                lam.append(lam_p)
+                break
+            del act[jb]
+            del lam[jb]
+    return u, 2
+
+
+def test_binary32_small_h_largen_near_pairs():
+    """The 20-robot configuration with near pairs (1024 envs, 30% starting with a pair at
+    0.18-0.20 m), the case the "h close to 0" re-solve was meant for: the active QPs met over
+    the first 100 steps of an FP64 oracle rollout, those whose active set keeps a pair row with
+    h < 1e-3 m^2 against a sample of the others, each solved in emulated binary32 and compared
+    with the oracle's binary64 minimiser."""
+    c = oracle.default_cfg(0, n_max=20, near_frac=0.3)
+    N, E, T = 20, 1024, 100
+    s = oracle.reset(c, 0, np.full(E, N, np.int32))
+    rng = np.random.default_rng(11)
+    near, other = [], []
+    pairs = [(a, q) for a in range(N) for q in range(a + 1, N)]
+    for t in range(T):
+        x, y, th = s.x.copy(), s.y.copy(), s.th.copy()
+        _, _, _, tr = oracle.step(c, 0, s, trace=True)
+        if t % 4:
+            continue  # every fourth step: QPs of the whole rollout, not one stretch of it
+        for e in np.nonzero(tr["qp"][:, 1] > 0)[0]:
+            if len(near) >= 60 and len(other) >= 60:
+                break
+            o = N * e
+            px = x[o:o + N] + c["l"] * np.cos(th[o:o + N])
+            py = y[o:o + N] + c["l"] * np.sin(th[o:o + N])
+            A, b = rows32(c, px.astype(F), py.astype(F), N)
+            u0 = tr["u_nom"][o:o + N].reshape(-1)
+            us = tr["u_star"][o:o + N].reshape(-1)
+            # the oracle's active pair rows: tight at its minimiser
+            hs = [(px[a] - px[q]) ** 2 + (py[a] - py[q]) ** 2 - c["r"] ** 2 for a, q in pairs]
+            slack = [np.dot(np.asarray(A[k], np.float64), us) - float(b[k]) for k in range(len(pairs))]
+            h_act = min([h for h, sl in zip(hs, slack) if abs(sl) < 1e-6] or [np.inf])
+            is_near = h_act < 1e-3
+            if is_near and len(near) >= 60:
+                continue
+            if not is_near and (len(other) >= 60 or rng.random() > 0.05):
+                continue
+            u, st = solve32_vec(A, b, u0.astype(F))
+            err = np.abs(u.astype(np.float64) - us).max()
+            (near if is_near else other).append((err, st, h_act))
+    en = np.array([e for e, _, _ in near])
+    eo = np.array([e for e, _, _ in other])
+    print(f"\nlargen near pairs: active pair h < 1e-3: {len(en)} QPs (min h "
+          f"{min(h for _, _, h in near):.2e}), max err {en.max():.2e}; others: {len(eo)} QPs, "
+          f"max err {eo.max():.2e}")
+    assert len(en) >= 30 and len(eo) >= 30
+    assert all(st == 0 for _, st, _ in near + other)
+    # both inside the 1e-5 control tolerance, near contact no worse than the others
+    assert eo.max() < 1e-5 and en.max() < 1e-5
+    assert en.max() <= max(2 * eo.max(), 1e-6)

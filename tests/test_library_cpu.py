@@ -47,3 +47,44 @@ def test_state_blob_parser_layout():
     assert st["n_envs"] == 2 and st["seed"] == 7
     assert st["x"].view(np.uint8)[0] == 1 and st["off"].view(np.uint8)[0] == 16
     assert st["gth"].view(np.uint8)[0] == 17 and len(st["gth"]) == T
+
+
+def test_every_declaration_is_documented():
+    """Each function include/rl.h declares carries a comment of its own: a block comment ending
+    on the line before its declaration (or before the group of declarations it heads), or one
+    on the declaration's own line."""
+    import os
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "rl.h")
+    lines = open(hdr).read().splitlines()
+    decl = re.compile(r"^\s*(?:rl_status|size_t|int32_t|const char\*|void)\s+(rl_[a-z_0-9]+)\s*\(")
+    seen = []
+    for i, ln in enumerate(lines):
+        m = decl.match(ln)
+        if not m:
+            continue
+        seen.append(m.group(1))
+        if "/*" in ln:
+            continue
+        j = i - 1
+        # a group of declarations under one comment, or a declaration continued over lines
+        while j >= 0 and (decl.match(lines[j]) or lines[j].startswith(" " * 8) or
+                          lines[j].strip().startswith("#define")):
+            j -= 1
+        assert j >= 0 and lines[j].rstrip().endswith("*/"), f"{m.group(1)} has no comment"
+    assert set(seen) >= {"rl_create", "rl_reset", "rl_step", "rl_rollout", "rl_destroy",
+                         "rl_rollout_noalloc", "rl_set_one_launch"}
+
+
+def test_boundary_calls_cite_the_paper():
+    """The calls that restate a step of the method name the passage they follow."""
+    import os
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "rl.h")).read()
+    for name, passage in (("rl_create", "Sec. 6.1"), ("rl_reset", "Sec. 6.1"),
+                          ("rl_step", "Dec-POMDP"), ("rl_rollout", "Sec. 4.1"),
+                          ("rl_policy_create", "App. A")):
+        k = hdr.index(f"rl_status {name}(")
+        comment = hdr[hdr.rindex("/*", 0, k):k]
+        assert passage in comment or passage in hdr[:hdr.index("#ifndef")], (name, passage)

@@ -32,15 +32,24 @@ def _buffers(T, rows, od, E, dt=torch.float32):
             torch.full((T, E), 7, dtype=torch.uint8, device="cuda"))
 
 
-@pytest.mark.parametrize("scenario,N,E,T", [(0, 4, 1024, 150), (1, 6, 300, 120)])
-def test_noalloc_matches_handle_rollout_twice(rl, scenario, N, E, T):
-    g = rl.config_default(scenario)
+# (scenario, robots, envs, steps, overrides).  The cases run in this order, so the Discovery case
+# (r_max 4) lays its resource segments over the Foraging case's (r_max 6) at shifted offsets,
+# the binary64 case reuses the array with 8-byte reals, and the last case takes a launch shape
+# of its own (the shuffle team kernel, 8 envs per warp, grid stride) from the configuration.
+CASES = [(0, 4, 1024, 150, {}), (1, 6, 300, 120, {}), (2, 5, 257, 110, dict(r_max=4, n_res_max=4)),
+         (0, 4, 200, 100, dict(precision=64)), (0, 4, 600, 60, dict(block_threads=128, warp_envs=8, small_variant=1))]
+
+
+@pytest.mark.parametrize("scenario,N,E,T,kw", CASES)
+def test_noalloc_matches_handle_rollout_twice(rl, scenario, N, E, T, kw):
+    g = rl.config_default(scenario, **kw)
     seeds = [11, 12]
     for call, seed in enumerate(seeds):
         env = rl.Env(g, E, N, seed)
-        ro, rr, rd = _buffers(T, E * N, env.obs_dim, E)
+        dt = env.dtype
+        ro, rr, rd = _buffers(T, E * N, env.obs_dim, E, dt)
         env.rollout(T, ro, rr, rd)
-        no, nr, nd = _buffers(T, E * N, env.obs_dim, E)
+        no, nr, nd = _buffers(T, E * N, env.obs_dim, E, dt)
         rl.rollout_noalloc(g, E, N, seed, T, no, nr, nd)
         torch.cuda.synchronize()
         assert (no - ro).abs().max().item() <= TOL, f"call {call}: observations differ"
@@ -52,7 +61,7 @@ def test_noalloc_matches_handle_rollout_twice(rl, scenario, N, E, T):
 def test_noalloc_rejects_oversized_batches(rl):
     g = rl.config_default(0)
     L = rl.lib()
-    limit = 8 << 20
+    limit = rl.noalloc_max_bytes()
     assert rl.noalloc_state_bytes(g, 4096, 4) <= limit
     E = 1 << 20
     assert rl.noalloc_state_bytes(g, E, 4) > limit
