@@ -71,6 +71,10 @@ WORKLOADS = {
 
 
 # the kernel each workload's rollout launches (one launch per bench step)
+# 4-robot binary32 Navigation kernels by the tuner's variant (1 shuffle, 2 gather, 3 split)
+NAV4_KERNELS = {1: "rl::env_kernel_small<1> (4-robot shuffle team kernel)",
+                2: "rl::env_kernel_small<2> (4-robot gather team kernel)",
+                3: "rl::env_kernel_split (4-robot shuffle teams, outputs in a second warp)"}
 KERNELS = {"nav": "rl::env_kernel_small<1> (4-robot shuffle team kernel)",
            "waypoint": "rl::env_kernel_small<2> (4-robot gather team kernel)",
            "uneven": "rl::env_kernel_multi (one persistent launch over all size classes)",
@@ -96,6 +100,15 @@ def _args():
     p.add_argument("--horizon", type=int, default=0,
                    help="override the workload's steps per rollout (small profiling cases)")
     return p.parse_args()
+
+
+def _kernel_name(workload: str, tuning) -> str:
+    """The kernel the rollout launches: the tuner's 4-robot variant where it picked one."""
+    if tuning and workload in ("nav", "waypoint", "waypoint_pose"):
+        for c in tuning.get("classes", []):
+            if c.get("nmax") == 4 and c.get("lanes") == 4 and c.get("variant") in NAV4_KERNELS:
+                return NAV4_KERNELS[c["variant"]]
+    return KERNELS.get(workload, "rl::env_kernel")
 
 
 def _rank_seed(rank: int) -> int:
@@ -153,6 +166,37 @@ def _peaks(key: str = "hbm_gbs", fallback: float = 6800.0):
         if key in d:
             return float(d[key]), "measured"
     return fallback, "fallback"
+
+
+def _fp32_flops(w, n_robots, qp_iters: float, env_steps: float):
+    """Algorithmic binary32 flops of Navigation env-steps (the method's arithmetic, counted from
+    its formulas, not from the instructions a kernel executes): per robot 85 + 4 (N - 1)
+    (projection 4, nominal velocity 4, two speed caps 12, noise 6, four arena rows 20, SI to
+    unicycle 7, wheel clip 8, Euler step and heading wrap 9, new projected point 4, reward term
+    11, relative poses of the observation 4 (N - 1)); per pair 21 (row 10, violation at u_nom 6,
+    collision test 5); per env N + 2 (team reward); per active-set iteration a rescan of every
+    row and the step, 6 P + 20 N + 8.  Square roots, sines and cosines are special-function
+    calls, not counted.  Returns (flops, flops per env-step) or (None, None) for scenarios with
+    resources."""
+    import numpy as np
+    if w["scenario"] != 0:
+        return None, None
+    N = np.asarray(n_robots, np.float64)
+    P = N * (N - 1) / 2
+    per_env = N * (85 + 4 * (N - 1)) + 21 * P + N + 2
+    steps_per_env = env_steps / len(N)
+    base = float(per_env.sum()) * steps_per_env
+    it_cost = float((6 * P + 20 * N + 8).mean())
+    flops = base + qp_iters * it_cost
+    return flops, flops / env_steps
+
+
+def _fp32_peak():
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 (FMA) x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz, src = _peaks("sm_max_mhz", 2070.0)
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz, src
 
 
 class Clocks:
@@ -467,9 +511,23 @@ def run_rollout(a):
     peak, peak_src = _peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": _ncu_traffic(a.workload),
-            "peak_source": peak_src, "kernel": KERNELS.get(a.workload, "rl::env_kernel"),
+            "peak_source": peak_src, "kernel": _kernel_name(a.workload, tuning),
             "algorithmic_bytes_per_launch": alg_bytes,
             "bytes_per_env_step": alg_bytes / (E * T)}
+
+    # ---- the same kernel against the FP32 CUDA-core peak (algorithmic flops, with the active-set
+    # iterations the counters recorded over the warm-up and timed rollouts)
+    iters_per_env_step = float(counters[:, 7].sum()) / env_steps_counted
+    fl, fl_es = _fp32_flops(w, n, iters_per_env_step * E * T, E * T)
+    if fl is not None:
+        pk, sms, mhz, src = _fp32_peak()
+        ach = fl / (kernel_ms / 1e3) / 1e12
+        roof_fp32 = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                     "frac": ach / pk, "flops_per_env_step": fl_es,
+                     "qp_iters_per_env_step": iters_per_env_step,
+                     "peak_source": f"{sms} SMs x 128 x 2 x {mhz:.0f} MHz ({src} max SM clock)"}
+    else:
+        roof_fp32 = None
 
     extra = {}
     if not a.no_plain and a.workload == "nav":
@@ -526,7 +584,7 @@ def run_rollout(a):
                 "robot_steps_per_s": value * rows / E,
                 "latency_ms": {"p50": float(np.percentile(per, 50)),
                                "p99": float(np.percentile(per, 99))},
-                "roofline": roof, "e2e": e2e,
+                "roofline": roof, "roofline_fp32": roof_fp32, "e2e": e2e,
                 "gpu_launches": a.steps,
                 "clocks": clk.summary(),
                 "qp": {"active_step_frac": float(counters[:, 3].sum()) / env_steps_counted,

@@ -94,7 +94,10 @@ typedef struct {
     int32_t small_variant;  /* 4-robot binary32 Navigation, scripted, without traces: 1 the team
                                kernel that reduces across lanes with shuffles (faster on large
                                batches), 2 the team kernel that publishes each robot's state in
-                               shared memory (lower latency per step); 0 picks by batch size */
+                               shared memory (lower latency per step), 3 the shuffle team kernel
+                               with the flags, reward and observations in a second warp per
+                               dynamics warp (position controller, spread launch); 0 picks by
+                               batch size */
     int32_t controller;     /* Navigation scripted nominal control: RL_CTRL_POSITION (go to the
                                goal point, k_si) or RL_CTRL_POSE (unicycle posture regulation to
                                the goal pose: position and goal heading, pose_k1..3) */
@@ -197,9 +200,9 @@ rl_status rl_set_one_launch(rl_env* env, int32_t on);
 
 /* End to end through host memory: upload h_state (rl_state_bytes() bytes, or NULL to keep the
    device state), run the T steps, and copy the trajectories to the host buffers (pinned memory
-   recommended; any may be NULL).  The steps run in up to 8 chunks, one launch each; each
-   chunk's slice of the trajectories is downloaded on a second stream while the next chunk
-   runs.  Same results as rl_rollout.  Returns after the copies completed. */
+   recommended; any may be NULL).  The steps run in up to 16 chunks, one launch each; each
+   chunk's slice of the observations is downloaded on a second stream while the next chunk
+   runs (rewards and done flags once, after the last chunk).  Same results as rl_rollout.  Returns after the copies completed. */
 rl_status rl_rollout_host(rl_env* env, const void* h_state, int32_t T, void* h_obs_traj,
                           void* h_rew_traj, uint8_t* h_done_traj);
 

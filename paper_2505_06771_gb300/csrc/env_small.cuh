@@ -695,8 +695,9 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
         const bool by_warp = FAST && wm != 0u;
         QPResult res = small_filter_all(tm, S, N, px, py, ux, uy, qc, usx, usy, by_warp);
         int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
-        if (by_warp) {
-            // rare QPs of the warp's envs, one env at a time by all live lanes
+        // rare QPs of the warp's envs (one vote when there are none), one env at a time by all
+        // live lanes
+        if (by_warp && __ballot_sync(wm, i == 0 && (res.status == 3 || (k.resolve_f64 && res.flag)))) {
             const int nl = __popc(wm);
             const int wl = threadIdx.x & 31;
             unsigned need = __ballot_sync(wm, i == 0 && res.status == 3);
@@ -762,7 +763,7 @@ __device__ void run_env_small(const LaunchArgs<float>& A, const Team<4>& tm,
                     }
                 }
             }
-        } else if (k.resolve_f64 && res.flag) {
+        } else if (!by_warp && k.resolve_f64 && res.flag) {
             const QPResult r64 = small_resolve_f64(tm, S, k, N, x, y, th, ux, uy);
             res.status = r64.status;
             res.q = r64.q;

@@ -2,6 +2,7 @@
 // the register-resident team kernel (4 lanes per env), and the generic shared-memory kernel with
 // 2 lanes per env (a tuner candidate).
 #include "env_nav4.cuh"
+#include "env_split.cuh"
 #include "env_thread.cuh"
 #include "launch.h"
 
@@ -22,6 +23,26 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     const bool fast = is_fast(a);
     int variant = a.variant;
     if (fast && a.k.controller != 0) variant = 2;  // the pose controller: gather kernel only
+    if (fast && variant == 3 && a.warp_envs <= 0 && max_blocks <= 0) {
+        // dynamics and output warps (env_split.cuh): one block of 4 + 4 warps per SM, the envs
+        // spread evenly over the dynamics warps when that leaves at most 8 per warp
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int blocks = std::min(sms, (a.n_list + 3) / 4);
+        if (blocks >= 1 && a.n_list <= 8 * 4 * blocks) {
+            const size_t sp = (size_t)32 * sizeof(TeamSmem<float, 4>);
+            e = cudaFuncSetAttribute(env_kernel_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sp);
+            if (e != cudaSuccess) return e;
+            LaunchArgs<float> b = a;
+            b.warp_envs = 0;
+            env_kernel_split<<<blocks, 256, sp, st>>>(b);
+            return cudaGetLastError();
+        }
+    }
+    if (variant == 3) variant = 1;  // beyond the split launch's reach: the shuffle team kernel
     if (fast && variant != 1 && variant != 2) {
         // auto: the gather kernel (lower latency per step) for small batches, the shuffle
         // kernel (fewer instructions per env-step) for large ones; measured on GB300, 4096

@@ -23,7 +23,7 @@ namespace {
 constexpr uint32_t kMagic = 0x31534C52u;  // "RLS1"
 constexpr uint32_t kVersion = 2u;
 constexpr int kSegs = 17;
-constexpr int kHostChunks = 8;  // rl_rollout_host: chunks of the rollout, one launch each
+constexpr int kHostChunks = 16;  // rl_rollout_host: chunks of the rollout, one launch each
 enum Seg { S_X = 0, S_Y, S_TH, S_GX, S_GY, S_LEVEL, S_T, S_EP, S_NRES, S_QX, S_QY, S_QLEVEL,
            S_QACTIVE, S_COUNTERS, S_NROB, S_OFF, S_GTH };
 
@@ -328,6 +328,9 @@ rl_status sync_and_take_status(rl_env* h, const char* what) {
     if (v == 0) return RL_OK;
     e = cudaMemsetAsync(h->d_status, 0, sizeof(v), h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
+    if (v & rl::kStatusWaitTimeout)
+        return fail(h, RL_ERR_TIMEOUT, std::string(what) +
+                                           ": a kernel's bounded wait ran out (its results are not valid)");
     if (v & rl::kStatusNonFiniteAction)
         return fail(h, RL_ERR_ARG, std::string(what) +
                                        ": a non-finite action reached the device (that robot's "
@@ -476,7 +479,7 @@ rl_status rl_create(const rl_config* cfg, int32_t n_envs, const int32_t* h_n_rob
         k.lanes = lanes;
         k.block_threads = nm <= 16 ? 64 : 32;
         k.warp_envs = cfg->warp_envs > 0 ? std::min(32, cfg->warp_envs) : 0;
-        k.variant = (cfg->small_variant == 1 || cfg->small_variant == 2) ? cfg->small_variant : 0;
+        k.variant = (cfg->small_variant >= 1 && cfg->small_variant <= 3) ? cfg->small_variant : 0;
         if (cfg->block_threads > 0) {
             if (cfg->block_threads % 32 != 0 || cfg->block_threads > 256) { rl_destroy(h); return RL_ERR_ARG; }
             k.block_threads = std::max(cfg->block_threads, lanes);
@@ -687,6 +690,8 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
                     cand[nc_][0] = 4; cand[nc_][1] = 128; cand[nc_][2] = we4[w]; cand[nc_][3] = var;
                     ++nc_;
                 }
+            // dynamics and output warps (spread launch only)
+            cand[nc_][0] = 4; cand[nc_][1] = 128; cand[nc_][2] = 0; cand[nc_][3] = 3; ++nc_;
             for (int w = 0; w < 3; ++w) {
                 cand[nc_][0] = 1; cand[nc_][1] = 4 * we1[w]; cand[nc_][2] = 0; cand[nc_][3] = 0;
                 ++nc_;
@@ -835,7 +840,7 @@ rl_status rl_rollout_host(rl_env* h, const void* h_state, int32_t T, void* h_obs
     if (T == 0) return RL_OK;
     // The rollout in chunks of steps, each chunk one launch on the handle's stream; after a
     // chunk's launch an event, on which the copy stream waits before downloading that chunk's
-    // slice of the trajectories.  Chunk k's download overlaps chunk k + 1's compute, so the call
+    // slice of the observations.  Chunk k's download overlaps chunk k + 1's compute, so the call
     // takes about max(compute, copy) instead of their sum.  Chunking gives the same results:
     // the kernels write the state back after a chunk and read it at the next.
     cudaError_t e = cudaSuccess;
@@ -858,13 +863,12 @@ rl_status rl_rollout_host(rl_env* h, const void* h_state, int32_t T, void* h_obs
         if (e == cudaSuccess && h_obs)
             e = cudaMemcpyAsync((char*)h_obs + t0 * ostep, (char*)d_obs + t0 * ostep,
                                 (t1 - t0) * ostep, cudaMemcpyDeviceToHost, h->copy_st);
-        if (e == cudaSuccess && h_rew)
-            e = cudaMemcpyAsync((char*)h_rew + t0 * rstep, (char*)d_rew + t0 * rstep,
-                                (t1 - t0) * rstep, cudaMemcpyDeviceToHost, h->copy_st);
-        if (e == cudaSuccess && h_done)
-            e = cudaMemcpyAsync(h_done + t0 * h->E, d_done + t0 * h->E, (t1 - t0) * h->E,
-                                cudaMemcpyDeviceToHost, h->copy_st);
     }
+    // rewards and done flags (a few percent of the bytes) in one copy each, after the last chunk
+    if (e == cudaSuccess && h_rew)
+        e = cudaMemcpyAsync(h_rew, d_rew, rb, cudaMemcpyDeviceToHost, h->copy_st);
+    if (e == cudaSuccess && h_done)
+        e = cudaMemcpyAsync(h_done, d_done, db, cudaMemcpyDeviceToHost, h->copy_st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "rollout_host download");

@@ -146,7 +146,7 @@ rl_status run(const rl_config& c, int E, int N, uint64_t seed, int T, void* obs,
     int bt = nmax_class <= 16 ? 64 : 32;
     if (c.block_threads > 0) bt = std::max(c.block_threads, lanes);
     a.warp_envs = c.warp_envs > 0 ? std::min(32, c.warp_envs) : 0;
-    a.variant = (c.small_variant == 1 || c.small_variant == 2) ? c.small_variant : 0;
+    a.variant = (c.small_variant >= 1 && c.small_variant <= 3) ? c.small_variant : 0;
     auto launch = [&](bool reset) -> cudaError_t {
         if constexpr (std::is_same<R, double>::value) {
             return rl::launch_f64(a, nmax_class, lanes, bt, 0, st, reset);

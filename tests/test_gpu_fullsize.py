@@ -4,8 +4,8 @@ through rl_rollout with T = 1 -- the benchmark's own call, its CUDA graph and th
 shape -- a few times, with the FP64 oracle stepped from the same states over the whole batch.
 
 Launch shapes: every candidate the autotuner can pick for the 4096 x 4 batch (the shuffle and
-gather team kernels with the spread launch or 2..8 envs per warp on a grid stride, one thread
-per env, two lanes per env), the shape the autotuner actually picks on this GPU, and for the
+gather team kernels with the spread launch or 2..8 envs per warp on a grid stride, the shuffle
+kernel with its outputs in a second warp, one thread per env, two lanes per env), the shape the autotuner actually picks on this GPU, and for the
 uneven batch the one persistent launch over every size class (the benchmark's launch) as well
 as one launch per class.
 
@@ -40,6 +40,7 @@ def _candidates_4robot():
     for var, name in ((1, "shuffle"), (2, "gather")):
         for we in (0, 2, 4, 6, 7, 8):
             out[f"{name}_we{we}"] = dict(lanes=4, block_threads=128, warp_envs=we, small_variant=var)
+    out["split"] = dict(lanes=4, block_threads=128, warp_envs=0, small_variant=3)
     for we in (8, 16, 32):
         out[f"thread_we{we}"] = dict(lanes=1, block_threads=4 * we)
     out["lanes2"] = dict(lanes=2, block_threads=64)
