@@ -87,6 +87,7 @@ struct StepIO {
 
 // Bits of the device status word.  Set by any lane, read and cleared by the host.
 constexpr int32_t kStatusNonFiniteAction = 1;
+constexpr int32_t kStatusWaitTimeout = 2;  // a bounded wait in a kernel ran out (policy kernel)
 
 // A non-finite policy action is replaced by zero (the robot's nominal velocity is zero, the
 // barrier QP still applies) and reported through the status word.
