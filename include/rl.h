@@ -293,15 +293,20 @@ rl_status rl_server_destroy(rl_server* srv);
        h1 = ReLU(W1 o + b1),  GRU(h1, h) -> h,  a = v_max tanh(Wo h + bo)
    with the GRU's gates r = sigma(Wi_r h1 + bi_r + Wh_r h + bh_r), z (likewise) and
    n = tanh(Wi_n h1 + bi_n + r * (Wh_n h + bh_n)), h <- (1 - z) n + z h.  The action a is the
-   robot's SI velocity (rl_step's policy actions).  The two dense layers before the gates run
-   on the tensor cores (cuBLASLt, bf16 operands: W1, b1, Wi, Wh and the inputs o, h1 and the
-   previous h are rounded to bf16, accumulation in binary32); gates, state and the head are
-   binary32, the gates' sigma and tanh from the hardware tanh approximation (relative error
-   about 2^-11).  The recurrent state is per robot, reset to zero when its env's episode ends.
-   Binary32 handles with policy actions (scripted = 0) only. */
+   robot's SI velocity (rl_step's policy actions).  Each policy step is one kernel on the
+   5th-generation tensor cores (tcgen05 MMA with the accumulators in tensor memory, operands
+   staged by TMA), 128 robots per CTA, with the observation's conversion, the first layer's bias
+   and ReLU, the gates, the new state and the head fused around the two products.  Operands of
+   the products are bf16 (W1, b1, Wi, Wh and the inputs o, h1 and the previous h rounded to
+   bf16, nearest-even), accumulation binary32; gates, state and the head are binary32, the
+   gates' sigma and tanh from the hardware tanh approximation (relative error about 2^-11).  The
+   recurrent state is per robot, reset to zero when its env's episode ends.  Binary32 handles
+   with policy actions (scripted = 0) and observations of at most 16 values (up to 4 robots) only.
+   A bounded wait inside the kernel that runs out raises the handle's status word (rl_sync then
+   returns RL_ERR_TIMEOUT). */
 typedef struct rl_policy rl_policy;
 
-/* Passage: App. A (policy architecture).  hidden: H, a multiple of 32 up to 512.  Host arrays, row-major: h_w1 [H][obs_dim], h_b1 [H],
+/* Passage: App. A (policy architecture).  hidden: H, a multiple of 64 up to 512.  Host arrays, row-major: h_w1 [H][obs_dim], h_b1 [H],
    h_wi [3H][H], h_bi [3H], h_wh [3H][H], h_bh [3H] (gate blocks in the order r, z, n),
    h_wo [2][H], h_bo [2].  Copies the weights to the device; the recurrent state starts at 0. */
 rl_status rl_policy_create(rl_env* env, int32_t hidden, const float* h_w1, const float* h_b1,

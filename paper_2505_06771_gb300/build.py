@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     if force or _stale(objs, LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcublasLt"],
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"],
                        check=True)
         os.replace(tmp, LIB)
     return LIB

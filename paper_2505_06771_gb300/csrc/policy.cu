@@ -1,21 +1,14 @@
 // policy.cu -- a recurrent policy evaluated on the GPU between environment steps (include/rl.h,
 // "Policy in the loop"), and rl_observe.
 //
-// One policy step over all robots of the batch:
-//   1. policy_input: the observation to bf16 (padded to a multiple of 16 columns); robots whose
-//      env ended its episode at the previous step get a zero recurrent state;
-//   2. tensor cores (cuBLASLt): h1 = ReLU(W1 o + b1), written in bf16 into the first half of
-//      each robot's [h1, h_prev] row;
-//   3. tensor cores (cuBLASLt): the gate pre-activations of r, z and the two halves of n from
-//      [h1, h_prev] with one block weight [[Wi_r, Wh_r], [Wi_z, Wh_z], [Wi_n, 0], [0, Wh_n]]
-//      (one GEMM with K = 2H instead of two);
-//   4. policy_gates: gates, the new state (binary32, and its bf16 copy for the next GEMM), and the
-//      two-output head reduced across a warp per robot;
-//   5. the environment step with those actions (rl_step).
-// The T steps are captured in a CUDA graph once and replayed.
-#include <cublasLt.h>
+// One policy step over all robots of the batch is one launch of policy_step_tc (policy_tc.cuh):
+// the observation in bf16, h1 = ReLU(W1 o + b1) on the tensor cores, the GRU's gate products
+// on the tensor cores (tcgen05, accumulators in tensor memory, operands by TMA), the gates, the
+// new state and the two-output head, for 128 robots per CTA; then the environment step with
+// those actions (rl_step).  The T steps are captured in a CUDA graph once and replayed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -25,73 +18,9 @@
 
 #include "../../include/rl.h"
 #include "internal.h"
+#include "policy_tc.cuh"
 
 namespace {
-
-constexpr size_t kLtWorkspace = size_t(32) << 20;
-
-__global__ void policy_input(const float* __restrict__ obs, int rows, int od, int odp, int H,
-                             const int32_t* __restrict__ row_env,
-                             const uint8_t* __restrict__ done_prev, __nv_bfloat16* __restrict__ x,
-                             __nv_bfloat16* __restrict__ cat, float* __restrict__ h) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int r = warp; r < rows; r += nwarps) {
-        for (int c = lane; c < odp; c += 32)
-            x[(size_t)r * odp + c] = __float2bfloat16_rn(c < od ? obs[(size_t)r * od + c] : 0.f);
-        if (done_prev && done_prev[row_env[r]]) {
-            for (int u = lane; u < H; u += 32) {
-                h[(size_t)r * H + u] = 0.f;
-                cat[(size_t)r * 2 * H + H + u] = __float2bfloat16_rn(0.f);
-            }
-        }
-    }
-}
-
-// Gate nonlinearities on the special-function unit: tanh.approx.f32 (relative error about
-// 2^-11, below the bf16 rounding of the GEMM operands) and sigma(v) = (1 + tanh(v / 2)) / 2.
-__device__ __forceinline__ float tanh_sfu(float v) {
-    float r;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ float sigmoid_f(float v) { return fmaf(0.5f, tanh_sfu(0.5f * v), 0.5f); }
-
-// One warp per robot: gates from the pre-activations g [rows][4H] (r, z, n from h1, n from
-// h_prev), the new state, and a = v_max tanh(Wo h + bo).
-__global__ void policy_gates(const float* __restrict__ g, const float* __restrict__ bias,
-                             const float* __restrict__ wo, const float* __restrict__ bo, int rows,
-                             int H, float vmax, float* __restrict__ h,
-                             __nv_bfloat16* __restrict__ cat, float* __restrict__ act) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int r = warp; r < rows; r += nwarps) {
-        const float* gr = g + (size_t)r * 4 * H;
-        float a0 = 0.f, a1 = 0.f;
-        for (int u = lane; u < H; u += 32) {
-            const float rg = sigmoid_f(gr[u] + bias[u]);
-            const float zg = sigmoid_f(gr[H + u] + bias[H + u]);
-            const float ng = tanh_sfu(gr[2 * H + u] + bias[2 * H + u] + rg * (gr[3 * H + u] + bias[3 * H + u]));
-            const float hp = h[(size_t)r * H + u];
-            const float hn = (1.f - zg) * ng + zg * hp;
-            h[(size_t)r * H + u] = hn;
-            cat[(size_t)r * 2 * H + H + u] = __float2bfloat16_rn(hn);
-            a0 += wo[u] * hn;
-            a1 += wo[H + u] * hn;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        }
-        if (lane == 0) {
-            act[2 * (size_t)r] = vmax * tanhf(a0 + bo[0]);
-            act[2 * (size_t)r + 1] = vmax * tanhf(a1 + bo[1]);
-        }
-    }
-}
 
 // Navigation observation of the current state, one thread per robot (the definition the step
 // kernels write after each step).
@@ -134,21 +63,16 @@ int grid_for(size_t work, int threads) {
 
 struct rl_policy {
     rl_env* env = nullptr;
-    int H = 0, od = 0, odp = 0, rows = 0, E = 0;
+    int H = 0, U = 0, od = 0, rows = 0, E = 0;
     float vmax = 0.f;
     cudaStream_t st = nullptr;
-    cublasLtHandle_t lt = nullptr;
-    __nv_bfloat16 *w1 = nullptr, *b1 = nullptr, *wcat = nullptr;
-    float *bias = nullptr, *wo = nullptr, *bo = nullptr;
-    __nv_bfloat16 *x = nullptr, *cat = nullptr;
-    float *g = nullptr, *h = nullptr, *act = nullptr;
+    __nv_bfloat16 *w1 = nullptr, *wcat = nullptr, *cat = nullptr;
+    float *b1 = nullptr, *bias = nullptr, *wo = nullptr, *bo = nullptr, *h = nullptr, *act = nullptr;
     int32_t* row_env = nullptr;
-    uint8_t* done0 = nullptr;  // [E] episode ended at the last step of the previous rollout
-    void* ws = nullptr;
-    cublasLtMatmulDesc_t d1 = nullptr, d2 = nullptr;
-    cublasLtMatrixLayout_t la1 = nullptr, lb1 = nullptr, lc1 = nullptr;
-    cublasLtMatrixLayout_t la2 = nullptr, lb2 = nullptr, lc2 = nullptr;
-    cublasLtMatmulAlgo_t algo1{}, algo2{};
+    int32_t* status = nullptr;   // the handle's device status word (a wait that ran out)
+    uint8_t* done0 = nullptr;    // [E] episode ended at the last step of the previous rollout
+    CUtensorMap tmA{}, tmB{};    // A = cat [rows][2H]; B = the gate weights [4H][2H]
+    size_t smem = 0;
     cudaGraphExec_t gexec = nullptr;
     int g_T = -1;
     const void* g_ptr[5] = {};
@@ -160,59 +84,41 @@ void policy_free(rl_policy* p) {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    if (p->d1) cublasLtMatmulDescDestroy(p->d1);
-    if (p->d2) cublasLtMatmulDescDestroy(p->d2);
-    for (cublasLtMatrixLayout_t l : {p->la1, p->lb1, p->lc1, p->la2, p->lb2, p->lc2})
-        if (l) cublasLtMatrixLayoutDestroy(l);
-    if (p->lt) cublasLtDestroy(p->lt);
-    void* bufs[] = {p->w1, p->b1, p->wcat, p->bias, p->wo, p->bo, p->x, p->cat, p->g,
-                    p->h, p->act, p->row_env, p->done0, p->ws};
+    void* bufs[] = {p->w1, p->b1, p->wcat, p->bias, p->wo, p->bo, p->cat, p->h, p->act,
+                    p->row_env, p->done0};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, p->st);
     if (p->st) cudaStreamSynchronize(p->st);
     delete p;
 }
 
-// One cuBLASLt matmul description: column-major D [m][n] = op_T(A) B with A stored [k][m].
-bool make_gemm(cublasLtHandle_t lt, int m, int n, int k, int lda, int ldb, int ldc,
-               cudaDataType_t ctype, cublasLtEpilogue_t epi, const void* bias,
-               cudaDataType_t bias_type,
-               cublasLtMatmulDesc_t* desc, cublasLtMatrixLayout_t* la, cublasLtMatrixLayout_t* lb,
-               cublasLtMatrixLayout_t* lc, cublasLtMatmulAlgo_t* algo, std::string& why) {
-    if (cublasLtMatmulDescCreate(desc, CUBLAS_COMPUTE_32F, CUDA_R_32F) != CUBLAS_STATUS_SUCCESS) {
-        why = "matmul description";
+// A 2-D bf16 tensor map [rows][cols] (row-major) with boxes of 64 columns x box_rows rows and
+// the 128-byte swizzle the MMA descriptors expect.
+bool make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows,
+              std::string& why) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            why = "cuTensorMapEncodeTiled unavailable";
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)rl::ptc::kKc, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        why = "tensor map encode failed (" + std::to_string((int)r) + ")";
         return false;
     }
-    const cublasOperation_t ta = CUBLAS_OP_T, tb = CUBLAS_OP_N;
-    cublasLtMatmulDescSetAttribute(*desc, CUBLASLT_MATMUL_DESC_TRANSA, &ta, sizeof(ta));
-    cublasLtMatmulDescSetAttribute(*desc, CUBLASLT_MATMUL_DESC_TRANSB, &tb, sizeof(tb));
-    cublasLtMatmulDescSetAttribute(*desc, CUBLASLT_MATMUL_DESC_EPILOGUE, &epi, sizeof(epi));
-    if (bias) {
-        cublasLtMatmulDescSetAttribute(*desc, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &bias, sizeof(bias));
-        cublasLtMatmulDescSetAttribute(*desc, CUBLASLT_MATMUL_DESC_BIAS_DATA_TYPE, &bias_type,
-                                       sizeof(bias_type));
-    }
-    if (cublasLtMatrixLayoutCreate(la, CUDA_R_16BF, k, m, lda) != CUBLAS_STATUS_SUCCESS ||
-        cublasLtMatrixLayoutCreate(lb, CUDA_R_16BF, k, n, ldb) != CUBLAS_STATUS_SUCCESS ||
-        cublasLtMatrixLayoutCreate(lc, ctype, m, n, ldc) != CUBLAS_STATUS_SUCCESS) {
-        why = "matrix layout";
-        return false;
-    }
-    cublasLtMatmulPreference_t pref = nullptr;
-    cublasLtMatmulPreferenceCreate(&pref);
-    size_t wsb = kLtWorkspace;
-    cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &wsb,
-                                         sizeof(wsb));
-    cublasLtMatmulHeuristicResult_t hr{};
-    int found = 0;
-    const cublasStatus_t s =
-        cublasLtMatmulAlgoGetHeuristic(lt, *desc, *la, *lb, *lc, *lc, pref, 1, &hr, &found);
-    cublasLtMatmulPreferenceDestroy(pref);
-    if (s != CUBLAS_STATUS_SUCCESS || found < 1) {
-        why = "no cuBLASLt algorithm for the policy GEMM";
-        return false;
-    }
-    *algo = hr.algo;
     return true;
 }
 
@@ -225,29 +131,30 @@ rl_status fail(rl_env* env, rl_policy* p, rl_status s, const std::string& msg) {
 // T policy steps enqueued on the handle's stream (captured into a graph by the caller).
 rl_status enqueue_rollout(rl_env* env, rl_policy* p, int T, const float* obs0, float* obs,
                           float* rew, uint8_t* done, float* act) {
-    const float one = 1.f, zero = 0.f;
     const size_t ob = (size_t)p->rows * p->od;
-    const int threads = 256;
-    const int gw = grid_for((size_t)p->rows * 32, threads);
+    rl::ptc::Params P;
+    P.row_env = p->row_env;
+    P.cat = p->cat;
+    P.h = p->h;
+    P.w1 = p->w1;
+    P.b1 = p->b1;
+    P.bias = p->bias;
+    P.wo = p->wo;
+    P.bo = p->bo;
+    P.status = p->status;
+    P.rows = p->rows;
+    P.od = p->od;
+    P.H = p->H;
+    P.U = p->U;
+    P.vmax = p->vmax;
+    const int grid = (p->rows + rl::ptc::kM - 1) / rl::ptc::kM;
     for (int t = 0; t < T; ++t) {
-        const float* o_in = (t == 0) ? obs0 : obs + (size_t)(t - 1) * ob;
-        const uint8_t* d_prev = (t == 0) ? p->done0 : done + (size_t)(t - 1) * p->E;
-        float* a_t = act ? act + (size_t)t * p->rows * 2 : p->act;
-        policy_input<<<gw, threads, 0, p->st>>>(o_in, p->rows, p->od, p->odp, p->H, p->row_env,
-                                                d_prev, p->x, p->cat, p->h);
+        P.obs = (t == 0) ? obs0 : obs + (size_t)(t - 1) * ob;
+        P.done_prev = (t == 0) ? p->done0 : done + (size_t)(t - 1) * p->E;
+        P.act = act ? act + (size_t)t * p->rows * 2 : p->act;
+        rl::ptc::policy_step_tc<<<grid, rl::ptc::kThreads, p->smem, p->st>>>(p->tmA, p->tmB, P);
         if (cudaGetLastError() != cudaSuccess) return RL_ERR_CUDA;
-        if (cublasLtMatmul(p->lt, p->d1, &one, p->w1, p->la1, p->x, p->lb1, &zero, p->cat,
-                           p->lc1, p->cat, p->lc1, &p->algo1, p->ws, kLtWorkspace,
-                           p->st) != CUBLAS_STATUS_SUCCESS)
-            return RL_ERR_CUDA;
-        if (cublasLtMatmul(p->lt, p->d2, &one, p->wcat, p->la2, p->cat, p->lb2, &zero, p->g,
-                           p->lc2, p->g, p->lc2, &p->algo2, p->ws, kLtWorkspace,
-                           p->st) != CUBLAS_STATUS_SUCCESS)
-            return RL_ERR_CUDA;
-        policy_gates<<<gw, threads, 0, p->st>>>(p->g, p->bias, p->wo, p->bo, p->rows, p->H,
-                                                p->vmax, p->h, p->cat, a_t);
-        if (cudaGetLastError() != cudaSuccess) return RL_ERR_CUDA;
-        const rl_status s = rl_step(env, a_t, obs + (size_t)t * ob,
+        const rl_status s = rl_step(env, P.act, obs + (size_t)t * ob,
                                     rew ? rew + (size_t)t * p->E : nullptr,
                                     done + (size_t)t * p->E);
         if (s != RL_OK) return s;
@@ -272,23 +179,34 @@ rl_status rl_policy_create(rl_env* env, int32_t hidden, const float* h_w1, const
     const rl_config& c = rl::env_config(env);
     if (c.precision != RL_PREC_F32 || c.scripted)
         return fail(env, nullptr, RL_ERR_ARG, "rl_policy_create: needs a binary32 handle that takes policy actions");
-    if (hidden < 32 || hidden > 512 || hidden % 32 != 0)
-        return fail(env, nullptr, RL_ERR_ARG, "rl_policy_create: hidden must be a multiple of 32 up to 512");
+    if (hidden < 64 || hidden > 512 || hidden % 64 != 0)
+        return fail(env, nullptr, RL_ERR_ARG, "rl_policy_create: hidden must be a multiple of 64 up to 512");
+    if (rl_obs_dim(env) > 16)
+        return fail(env, nullptr, RL_ERR_ARG, "rl_policy_create: observations of at most 16 values (4 robots)");
     rl_policy* p = new (std::nothrow) rl_policy();
     if (!p) return RL_ERR_OOM;
     p->env = env;
     p->H = hidden;
+    // hidden units per block of gate accumulators (shared memory: 2 stages of 3 gate slots of
+    // U x 64 bf16 each, beside the resident A of H <= 256)
+    p->U = (hidden == 128 || (hidden > rl::ptc::kResidentH && hidden % 128 == 0)) ? 128 : 64;
     p->od = rl_obs_dim(env);
-    p->odp = (p->od + 15) / 16 * 16;
     p->rows = rl_total_robots(env);
     p->E = rl_n_envs(env);
     p->vmax = (float)c.vmax;
     p->st = rl::env_stream(env);
-    const int H = p->H, od = p->od, odp = p->odp, rows = p->rows;
-    // weights on the host in their device layouts
-    std::vector<float> w1((size_t)H * odp, 0.f), wcat((size_t)4 * H * 2 * H, 0.f), bias(4 * H);
+    p->smem = rl::ptc::smem_bytes(p->U, p->H);
+    {
+        rl::LaunchArgs<float> a;
+        rl::env_args_f32(env, a);
+        p->status = a.io.status;  // the policy kernel reports into the handle's status word
+    }
+    const int H = p->H, od = p->od, rows = p->rows;
+    // weights on the host in their device layouts: W1 [H][16] (observation padded), the gate
+    // weights [4H][2H] = [[Wi_r, Wh_r], [Wi_z, Wh_z], [Wi_n, 0], [0, Wh_n]], biases [4H]
+    std::vector<float> w1((size_t)H * 16, 0.f), wcat((size_t)4 * H * 2 * H, 0.f), bias(4 * H), b1(H);
     for (int u = 0; u < H; ++u)
-        for (int q = 0; q < od; ++q) w1[(size_t)u * odp + q] = h_w1[(size_t)u * od + q];
+        for (int q = 0; q < od; ++q) w1[(size_t)u * 16 + q] = h_w1[(size_t)u * od + q];
     for (int gte = 0; gte < 3; ++gte)
         for (int u = 0; u < H; ++u) {
             const size_t src = (size_t)(gte * H + u) * H;
@@ -304,28 +222,31 @@ rl_status rl_policy_create(rl_env* env, int32_t hidden, const float* h_w1, const
         bias[H + u] = h_bi[H + u] + h_bh[H + u];
         bias[2 * H + u] = h_bi[2 * H + u];
         bias[3 * H + u] = h_bh[2 * H + u];
+        // the first layer's bias enters in bf16 (rounded to nearest even)
+        uint32_t bits;
+        std::memcpy(&bits, &h_b1[u], 4);
+        bits = (bits + 0x7FFFu + ((bits >> 16) & 1u)) & 0xFFFF0000u;
+        std::memcpy(&b1[u], &bits, 4);
     }
     std::vector<int32_t> row_env(rows);
     const std::vector<int32_t>& off = rl::env_offsets(env);
     for (int e = 0; e < p->E; ++e)
         for (int r = off[e]; r < off[e + 1]; ++r) row_env[r] = e;
-    // device buffers
+    // device buffers (the state per tile of 128 robots, unit-major)
+    const size_t h_bytes = (size_t)((rows + rl::ptc::kM - 1) / rl::ptc::kM) * rl::ptc::kM * H * 4;
     float* staging = nullptr;
     const size_t stage_n = std::max(w1.size(), wcat.size());
     bool ok = cudaMallocAsync((void**)&p->w1, w1.size() * 2, p->st) == cudaSuccess &&
-              cudaMallocAsync((void**)&p->b1, (size_t)H * 2, p->st) == cudaSuccess &&
+              cudaMallocAsync((void**)&p->b1, (size_t)H * 4, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->wcat, wcat.size() * 2, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->bias, bias.size() * 4, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->wo, (size_t)2 * H * 4, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->bo, 2 * 4, p->st) == cudaSuccess &&
-              cudaMallocAsync((void**)&p->x, (size_t)rows * odp * 2, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->cat, (size_t)rows * 2 * H * 2, p->st) == cudaSuccess &&
-              cudaMallocAsync((void**)&p->g, (size_t)rows * 4 * H * 4, p->st) == cudaSuccess &&
-              cudaMallocAsync((void**)&p->h, (size_t)rows * H * 4, p->st) == cudaSuccess &&
+              cudaMallocAsync((void**)&p->h, h_bytes, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->act, (size_t)rows * 2 * 4, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->row_env, (size_t)rows * 4, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&p->done0, (size_t)p->E, p->st) == cudaSuccess &&
-              cudaMallocAsync(&p->ws, kLtWorkspace, p->st) == cudaSuccess &&
               cudaMallocAsync((void**)&staging, stage_n * 4, p->st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -338,35 +259,33 @@ rl_status rl_policy_create(rl_env* env, int32_t hidden, const float* h_w1, const
         to_bf16<<<grid_for(n, 256), 256, 0, p->st>>>(staging, dst, n);
         return cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(p->st) == cudaSuccess;
     };
-    ok = up_bf16(w1.data(), w1.size(), p->w1) && up_bf16(h_b1, H, p->b1) &&
-         up_bf16(wcat.data(), wcat.size(), p->wcat) &&
+    ok = up_bf16(w1.data(), w1.size(), p->w1) && up_bf16(wcat.data(), wcat.size(), p->wcat) &&
+         cudaMemcpyAsync(p->b1, b1.data(), (size_t)H * 4, cudaMemcpyHostToDevice, p->st) == cudaSuccess &&
          cudaMemcpyAsync(p->bias, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice, p->st) == cudaSuccess &&
          cudaMemcpyAsync(p->wo, h_wo, (size_t)2 * H * 4, cudaMemcpyHostToDevice, p->st) == cudaSuccess &&
          cudaMemcpyAsync(p->bo, h_bo, 2 * 4, cudaMemcpyHostToDevice, p->st) == cudaSuccess &&
          cudaMemcpyAsync(p->row_env, row_env.data(), (size_t)rows * 4, cudaMemcpyHostToDevice, p->st) == cudaSuccess &&
-         cudaMemsetAsync(p->h, 0, (size_t)rows * H * 4, p->st) == cudaSuccess &&
+         cudaMemsetAsync(p->h, 0, h_bytes, p->st) == cudaSuccess &&
          cudaMemsetAsync(p->cat, 0, (size_t)rows * 2 * H * 2, p->st) == cudaSuccess &&
          cudaMemsetAsync(p->done0, 0, (size_t)p->E, p->st) == cudaSuccess &&
          cudaStreamSynchronize(p->st) == cudaSuccess;
     cudaFreeAsync(staging, p->st);
     if (!ok) return fail(env, p, RL_ERR_CUDA, "rl_policy_create: upload");
-    if (cublasLtCreate(&p->lt) != CUBLAS_STATUS_SUCCESS)
-        return fail(env, p, RL_ERR_CUDA, "rl_policy_create: cuBLASLt");
     std::string why;
-    // h1 (bf16, into the first H rows of each [2H] column of cat) = ReLU(W1 x + b1)
-    if (!make_gemm(p->lt, H, rows, odp, odp, odp, 2 * H, CUDA_R_16BF, CUBLASLT_EPILOGUE_RELU_BIAS,
-                   p->b1, CUDA_R_16BF, &p->d1, &p->la1, &p->lb1, &p->lc1, &p->algo1, why) ||
-        !make_gemm(p->lt, 4 * H, rows, 2 * H, 2 * H, 2 * H, 4 * H, CUDA_R_32F,
-                   CUBLASLT_EPILOGUE_DEFAULT, nullptr, CUDA_R_32F, &p->d2, &p->la2, &p->lb2,
-                   &p->lc2, &p->algo2, why))
+    if (!make_map(&p->tmA, p->cat, 2 * (uint64_t)H, (uint64_t)rows, rl::ptc::kM, why) ||
+        !make_map(&p->tmB, p->wcat, 2 * (uint64_t)H, 4 * (uint64_t)H, (uint32_t)p->U, why))
         return fail(env, p, RL_ERR_CUDA, "rl_policy_create: " + why);
+    if (cudaFuncSetAttribute(rl::ptc::policy_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)p->smem) != cudaSuccess)
+        return fail(env, p, RL_ERR_CUDA, "rl_policy_create: shared memory");
     *out = p;
     return RL_OK;
 }
 
 rl_status rl_policy_reset_hidden(rl_policy* p) {
     if (!p) return RL_ERR_ARG;
-    if (cudaMemsetAsync(p->h, 0, (size_t)p->rows * p->H * 4, p->st) != cudaSuccess ||
+    const size_t h_bytes = (size_t)((p->rows + rl::ptc::kM - 1) / rl::ptc::kM) * rl::ptc::kM * p->H * 4;
+    if (cudaMemsetAsync(p->h, 0, h_bytes, p->st) != cudaSuccess ||
         cudaMemsetAsync(p->cat, 0, (size_t)p->rows * 2 * p->H * 2, p->st) != cudaSuccess ||
         cudaMemsetAsync(p->done0, 0, (size_t)p->E, p->st) != cudaSuccess)
         return RL_ERR_CUDA;
@@ -401,7 +320,8 @@ rl_status rl_policy_rollout(rl_env* env, rl_policy* p, int32_t T, const void* d_
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             p->gexec = nullptr;
-            rl::env_set_error(env, "policy rollout graph instantiate");
+            rl::env_set_error(env, std::string("policy rollout graph instantiate: ") +
+                                       cudaGetErrorString(e));
             return RL_ERR_CUDA;
         }
         p->g_T = T;
