@@ -186,17 +186,20 @@ rl_status rl_rollout_plain(rl_env* env, int32_t T, void* d_obs_traj, void* d_rew
    state, restored afterwards) for every launch shape -- lanes per environment and threads per
    block for each robot-count class, and for an uneven batch one persistent launch over all
    classes against one launch per class -- and keeps the fastest for later rollouts.
-   h_choice (NULL or 26 ints): [one-launch flag, then per robot-count class (nmax, lanes,
-   block threads, envs per warp, 4-robot kernel variant)].
+   h_choice (NULL or 26 ints): [class launch mode (rl_set_class_launch), then per robot-count
+   class (nmax, lanes, block threads, envs per warp, 4-robot kernel variant)].
    The probes write their trajectories to scratch memory the call allocates and frees.
    Synchronises the stream.  RL_ERR_STATE if the handle is not scripted. */
 rl_status rl_tune(rl_env* env, int32_t T_probe, int32_t* h_choice);
 
-/* Uneven binary32 batches (more than one robot-count class): on = 1 runs rl_rollout as one
-   persistent launch over every class (the default, and rl_tune's candidate), on = 0 as one
-   launch per class.  Same results either way up to rounding.  RL_ERR_STATE for a batch with one
-   class or a binary64 handle, RL_ERR_ARG for other values of on. */
-rl_status rl_set_one_launch(rl_env* env, int32_t on);
+/* Uneven binary32 batches (more than one robot-count class): how rl_rollout launches the
+   classes.  mode 1: one persistent launch over every class (the default); 0: one launch per
+   class, in sequence; 2: one launch per class, each on its own stream forked from and joined
+   back to the handle's stream, so that the classes run at the same time (parallel branches of
+   the rollout's CUDA graph).  rl_tune picks among the three.  Same results in every mode up to
+   rounding.  RL_ERR_STATE for a batch with one class or a binary64 handle, RL_ERR_ARG for other
+   modes. */
+rl_status rl_set_class_launch(rl_env* env, int32_t mode);
 
 /* End to end through host memory: upload h_state (rl_state_bytes() bytes, or NULL to keep the
    device state), run the T steps, and copy the trajectories to the host buffers (pinned memory

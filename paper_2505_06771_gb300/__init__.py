@@ -116,7 +116,7 @@ def lib():
         L.rl_destroy.argtypes = [vp]
         L.rl_destroy.restype = None
         L.rl_tune.argtypes = [vp, i32, vp]
-        L.rl_set_one_launch.argtypes = [vp, i32]
+        L.rl_set_class_launch.argtypes = [vp, i32]
         L.rl_server_create.argtypes = [ctypes.POINTER(RLConfig), sz, i32, ctypes.POINTER(vp)]
         L.rl_server_submit.argtypes = [vp, ctypes.POINTER(RLRequest),
                                        ctypes.POINTER(ctypes.c_uint64)]
@@ -271,15 +271,16 @@ class Env:
         out = np.zeros(26, np.int32)
         self._check(self._L.rl_tune(self._h, T_probe, out.ctypes.data), "rl_tune")
         self.lanes = int(self._L.rl_lanes(self._h))
-        return {"one_launch": bool(out[0]),
+        return {"one_launch": bool(out[0] == 1), "class_launch": int(out[0]),
                 "classes": [dict(nmax=int(out[1 + 5 * c]), lanes=int(out[2 + 5 * c]),
                                  block_threads=int(out[3 + 5 * c]),
                                  warp_envs=int(out[4 + 5 * c]), variant=int(out[5 + 5 * c]))
                             for c in range(5) if out[1 + 5 * c] > 0]}
 
-    def set_one_launch(self, on: bool):
-        """rl_set_one_launch: uneven batches as one persistent launch (True) or one per class."""
-        self._check(self._L.rl_set_one_launch(self._h, 1 if on else 0), "rl_set_one_launch")
+    def set_class_launch(self, mode: int):
+        """rl_set_class_launch: uneven batches as one persistent launch (1), one launch per class
+        in sequence (0) or one per class on parallel streams (2)."""
+        self._check(self._L.rl_set_class_launch(self._h, int(mode)), "rl_set_class_launch")
 
     def state_bytes(self) -> int:
         return int(self._L.rl_state_bytes(self._h))

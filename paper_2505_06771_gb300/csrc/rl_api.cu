@@ -68,8 +68,11 @@ struct rl_env {
     size_t scratch_bytes = 0;
     cudaStream_t copy_st = nullptr;
     cudaEvent_t chunk_ev[kHostChunks] = {};
-    // one persistent launch over all classes (binary32, uneven batches)
+    // uneven batches: 1 one persistent launch over all classes (binary32), 0 one launch per class
+    // in sequence, 2 one launch per class on parallel streams (parallel branches of the graph)
     int use_multi = 0;
+    cudaStream_t side[rl::kNumClasses] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[rl::kNumClasses] = {};
     int n_items = 0;
     int4* d_items = nullptr;
     unsigned* d_head = nullptr;
@@ -204,18 +207,45 @@ void fill_args(const rl_env* h, rl::LaunchArgs<R>& a) {
 
 template <typename R>
 cudaError_t launch_class(const rl_env* h, const Class& c, rl::LaunchArgs<R> a, bool reset,
-                         int max_blocks = 0) {
+                         int max_blocks = 0, cudaStream_t st = nullptr) {
+    if (!st) st = h->st;
     a.env_list = h->d_lists + c.begin;
     a.n_list = c.count;
     a.warp_envs = c.warp_envs;
     a.variant = c.variant;
     if constexpr (std::is_same<R, double>::value) {
-        return rl::launch_f64(a, c.nmax, c.lanes, c.block_threads, max_blocks, h->st, reset);
+        return rl::launch_f64(a, c.nmax, c.lanes, c.block_threads, max_blocks, st, reset);
     } else {
         if (c.nmax == 4)
-            return rl::launch_f32_small(a, c.lanes, c.block_threads, max_blocks, h->st, reset);
-        return rl::launch_f32_large(a, c.nmax, c.lanes, c.block_threads, max_blocks, h->st, reset);
+            return rl::launch_f32_small(a, c.lanes, c.block_threads, max_blocks, st, reset);
+        return rl::launch_f32_large(a, c.nmax, c.lanes, c.block_threads, max_blocks, st, reset);
     }
+}
+
+// Side streams and events of the parallel per-class launch, made on first use.
+cudaError_t ensure_side_streams(rl_env* h) {
+    if (h->fork_ev) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+    for (int c = 0; c < rl::kNumClasses && e == cudaSuccess; ++c) {
+        e = cudaStreamCreateWithFlags(&h->side[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev[c], cudaEventDisableTiming);
+    }
+    return e;
+}
+
+// One launch per class, each on its own stream forked from and joined back to the handle's
+// stream: the classes' kernels run at the same time (in a captured graph: parallel branches).
+template <typename R>
+rl_status run_parallel(rl_env* h, rl::LaunchArgs<R>& a, const char* what) {
+    cudaError_t e = ensure_side_streams(h);
+    if (e == cudaSuccess) e = cudaEventRecord(h->fork_ev, h->st);
+    for (int i = 0; i < h->ncls && e == cudaSuccess; ++i) {
+        e = cudaStreamWaitEvent(h->side[i], h->fork_ev, 0);
+        if (e == cudaSuccess) e = launch_class<R>(h, h->cls[i], a, false, 0, h->side[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(h->join_ev[i], h->side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st, h->join_ev[i], 0);
+    }
+    return e == cudaSuccess ? RL_OK : cuda_fail(h, e, what);
 }
 
 template <typename R>
@@ -263,7 +293,7 @@ rl_status do_rollout_launch(rl_env* h, int T, void* obs, void* rew, uint8_t* don
     a.io.reward = (R*)rew;
     a.io.done = done;
     if constexpr (std::is_same<R, float>::value) {
-        if (h->use_multi && h->n_items > 0) {
+        if (h->use_multi == 1 && h->n_items > 0) {
             rl::MultiArgs m;
             std::memset(&m, 0, sizeof(m));
             m.a = a;
@@ -282,6 +312,7 @@ rl_status do_rollout_launch(rl_env* h, int T, void* obs, void* rew, uint8_t* don
             return RL_OK;
         }
     }
+    if (h->use_multi == 2 && h->ncls > 1) return run_parallel<R>(h, a, "rollout (parallel classes)");
     return run_all(h, a, false, "rollout");
 }
 
@@ -292,7 +323,7 @@ rl_status do_rollout_returns(rl_env* h, int T, void* ret) {
     a.T = T;
     a.io.ret = (R*)ret;
     if constexpr (std::is_same<R, float>::value) {
-        if (h->use_multi && h->n_items > 0) {
+        if (h->use_multi == 1 && h->n_items > 0) {
             rl::MultiArgs m;
             std::memset(&m, 0, sizeof(m));
             m.a = a;
@@ -310,6 +341,7 @@ rl_status do_rollout_returns(rl_env* h, int T, void* ret) {
             return e == cudaSuccess ? RL_OK : cuda_fail(h, e, "serving rollout");
         }
     }
+    if (h->use_multi == 2 && h->ncls > 1) return run_parallel<R>(h, a, "serving rollout");
     return run_all(h, a, false, "serving rollout");
 }
 
@@ -720,16 +752,18 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
         h->ncls = nc;
         h->cls[c] = pick;
     }
-    // uneven batches: one launch over every class, or one launch per class
+    // uneven batches: one launch over every class, one launch per class in sequence, or one per
+    // class on parallel streams
     if (st == RL_OK && h->n_items > 0) {
-        float per_class = 0.f, one = 0.f;
-        h->use_multi = 0;
-        st = probe(per_class);
-        if (st == RL_OK) {
-            h->use_multi = 1;
-            st = probe(one);
+        float t_mode[3] = {0.f, 0.f, 0.f};
+        for (int m = 0; m < 3 && st == RL_OK; ++m) {
+            h->use_multi = m;
+            st = probe(t_mode[m]);
         }
-        h->use_multi = (st == RL_OK && one <= per_class) ? 1 : 0;
+        int best_m = 1;
+        for (int m = 0; m < 3; ++m)
+            if (t_mode[m] < t_mode[best_m]) best_m = m;
+        h->use_multi = st == RL_OK ? best_m : keep_multi;
     } else {
         h->use_multi = keep_multi;
     }
@@ -755,12 +789,12 @@ rl_status rl_tune(rl_env* h, int32_t T_probe, int32_t* h_choice) {
     return RL_OK;
 }
 
-rl_status rl_set_one_launch(rl_env* h, int32_t on) {
-    if (!h || (on != 0 && on != 1)) return RL_ERR_ARG;
+rl_status rl_set_class_launch(rl_env* h, int32_t mode) {
+    if (!h || mode < 0 || mode > 2) return RL_ERR_ARG;
     if (h->n_items == 0)
-        return fail(h, RL_ERR_STATE, "rl_set_one_launch: the batch has one size class (or is binary64)");
-    if (h->use_multi != on) drop_graph(h);
-    h->use_multi = on;
+        return fail(h, RL_ERR_STATE, "rl_set_class_launch: the batch has one size class (or is binary64)");
+    if (h->use_multi != mode) drop_graph(h);
+    h->use_multi = mode;
     return RL_OK;
 }
 
@@ -900,6 +934,11 @@ void rl_destroy(rl_env* h) {
     drop_graph(h);
     // stream-ordered frees: no device-wide synchronisation
     if (h->d_scratch) cudaFreeAsync(h->d_scratch, h->st);
+    for (int c = 0; c < rl::kNumClasses; ++c) {
+        if (h->side[c]) cudaStreamDestroy(h->side[c]);
+        if (h->join_ev[c]) cudaEventDestroy(h->join_ev[c]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->copy_st) {
         cudaStreamSynchronize(h->copy_st);
         for (int k = 0; k < kHostChunks; ++k)

@@ -67,7 +67,7 @@ def _run(rl, g, o, n, warm, tune=False, one_launch=None, steps=3, seed=1000):
     env = rl.Env(g, E, n, seed)
     choice = env.tune(50) if tune else None
     if one_launch is not None:
-        env.set_one_launch(one_launch)
+        env.set_class_launch(one_launch)
     R = env.total_robots
     env.rollout(warm)  # into a random state (no trajectory kept)
     obs = torch.empty(1, R, env.obs_dim, device="cuda")
@@ -121,7 +121,7 @@ def test_full_size_tuned_launch(rl, case):
     _check(worst)
 
 
-@pytest.mark.parametrize("one_launch", [True, False])
+@pytest.mark.parametrize("one_launch", [1, 0, 2])
 def test_uneven8192_one_launch_and_per_class(rl, one_launch):
     """The uneven batch through the one persistent launch over every size class (the kernel the
     uneven benchmark times) and through one launch per class, each against the oracle."""

@@ -403,7 +403,7 @@ def test_free_run_uneven_one_launch_100_steps(rl, scenario):
     g, o = make_pair(scenario, 10)
     E, seed, T = len(n), 17, 100
     env = rl.Env(g, E, n, seed)
-    env.set_one_launch(True)
+    env.set_class_launch(1)
     b = _alloc(env, T)
     env.rollout(T, **b)
     torch.cuda.synchronize()
@@ -602,6 +602,28 @@ def test_uneven_one_launch_matches_steps(rl, scenario):
     assert worst < 1e-5
     a.close()
     b.close()
+
+
+def test_uneven_parallel_classes_equal_sequential(rl):
+    """One launch per class on parallel streams gives the same trajectories and state as one
+    launch per class in sequence, bit for bit (the same kernels on the same data)."""
+    from synth_inputs import uneven_robot_counts
+    n = uneven_robot_counts(9, 700, 2, 10)
+    g, _ = make_pair(1, 10, episode_len=30)
+    T = 45
+    outs = []
+    for mode in (0, 2):
+        env = rl.Env(g, 700, n, 13)
+        env.set_class_launch(mode)
+        b = _alloc(env, T)
+        env.rollout(T, **b)
+        env.rollout(T, **b)  # the cached graph replayed
+        torch.cuda.synchronize()
+        outs.append((b, env.get_state()))
+        env.close()
+    (b0, s0), (b2, s2) = outs
+    assert torch.equal(b0["obs"], b2["obs"]) and torch.equal(b0["reward"], b2["reward"])
+    assert torch.equal(b0["done"], b2["done"]) and s0 == s2
 
 
 def test_tuner_keeps_state_and_results(rl):

@@ -74,7 +74,7 @@ def test_every_declaration_is_documented():
             j -= 1
         assert j >= 0 and lines[j].rstrip().endswith("*/"), f"{m.group(1)} has no comment"
     assert set(seen) >= {"rl_create", "rl_reset", "rl_step", "rl_rollout", "rl_destroy",
-                         "rl_rollout_noalloc", "rl_set_one_launch"}
+                         "rl_rollout_noalloc", "rl_set_class_launch"}
 
 
 def test_boundary_calls_cite_the_paper():
