@@ -96,6 +96,10 @@ def _args():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form leg")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    p.add_argument("--variant", type=int, default=0,
+                   help="4-robot Navigation: fix the kernel (1 shuffle, 2 gather, 3 split: the "
+                        "tuner's pick on GB300) with the spread launch and skip the tuner, so "
+                        "that runs under a profiler time the same kernel")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     p.add_argument("--horizon", type=int, default=0,
                    help="override the workload's steps per rollout (small profiling cases)")
@@ -103,9 +107,9 @@ def _args():
 
 
 def _kernel_name(workload: str, tuning) -> str:
-    """The kernel the rollout launches: the tuner's 4-robot variant where it picked one."""
+    """The kernel the rollout launches: the tuner's (or the fixed) 4-robot variant."""
     if tuning and workload in ("nav", "waypoint", "waypoint_pose"):
-        for c in tuning.get("classes", []):
+        for c in tuning.get("classes", []) + ([tuning["fixed"]] if "fixed" in tuning else []):
             if c.get("nmax") == 4 and c.get("lanes") == 4 and c.get("variant") in NAV4_KERNELS:
                 return NAV4_KERNELS[c["variant"]]
     return KERNELS.get(workload, "rl::env_kernel")
@@ -458,6 +462,8 @@ def run_rollout(a):
     n = _robots(w)
     stream = torch.cuda.Stream()
     g = rl.config_default(w["scenario"], precision=w["precision"], **_cfg_overrides(w))
+    if a.variant:
+        g.update(small_variant=a.variant, block_threads=128, warp_envs=0)
     fdt = torch.float64 if w["precision"] == 64 else torch.float32
     esz = 8 if w["precision"] == 64 else 4
     with torch.cuda.stream(stream):
@@ -468,7 +474,10 @@ def run_rollout(a):
         done = torch.empty(T, E, dtype=torch.uint8, device="cuda")
     stream.synchronize()
     tuning = None
-    if not a.no_tune and w["precision"] == 32:
+    if a.variant:
+        tuning = {"fixed": {"nmax": 4, "lanes": 4, "block_threads": 128, "warp_envs": 0,
+                            "variant": a.variant}}
+    elif not a.no_tune and w["precision"] == 32:
         # probes of up to 1000 steps: the slow tail of a rollout (a few envs whose robots stay
         # jammed for many steps) decides its time and does not show in short probes
         tuning = env.tune(min(1000, T))
