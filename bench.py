@@ -108,7 +108,9 @@ def _args():
 
 def _kernel_name(workload: str, tuning) -> str:
     """The kernel the rollout launches: the tuner's (or the fixed) 4-robot variant."""
-    if tuning and workload in ("nav", "waypoint", "waypoint_pose"):
+    if workload == "waypoint_pose":
+        return NAV4_KERNELS[2]  # the pose controller runs in the gather kernel only
+    if tuning and workload in ("nav", "waypoint"):
         for c in tuning.get("classes", []) + ([tuning["fixed"]] if "fixed" in tuning else []):
             if c.get("nmax") == 4 and c.get("lanes") == 4 and c.get("variant") in NAV4_KERNELS:
                 return NAV4_KERNELS[c["variant"]]

@@ -1,5 +1,5 @@
-// env_split.cuh -- the 4-robot Navigation rollout (binary32, scripted position control, no
-// traces) with the per-step outputs taken off the dynamics' dependency chain.
+// env_split.cuh -- the 4-robot Navigation rollout (binary32, scripted position control or policy
+// actions, no traces) with the per-step outputs taken off the dynamics' dependency chain.
 //
 // Same method and results (up to rounding) as run_env_small<true>.  Each block holds 8 warps on
 // one SM: warps 0-3 run the dynamics of their envs (nominal velocity, barrier QP, unicycle step,
@@ -78,34 +78,43 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
         float npx = 0.f, npy = 0.f, dterm = 0.f;
         int done = 0, oob_i = 0;
         if (live) {
-            // ---- projected point and nominal SI velocity (go to goal, cap, noise, cap)
+            // ---- projected point and nominal SI velocity: the policy's action, or go to goal,
+            // cap, noise; then the cap
             const float px = x + k.l * cs, py = y + k.l * sn;
-            float ux = k.k_si * (gx - px), uy = k.k_si * (gy - py);
-            cap_fast(ux, uy, k.vmax);
-            uint32_t wx, wy;
-            if (nz_ep == ep && nz_t + 1 == t) {
-                wx = nz_nx;
-                wy = nz_ny;
-                nz_t = -2;
+            float ux, uy;
+            if (A.io.actions) {
+                ux = A.io.actions[2 * row];
+                uy = A.io.actions[2 * row + 1];
+                screen_action(A.io.status, ux, uy);
             } else {
-                // robots 2m and 2m + 1 share the Philox block (pair m, step t): their lanes draw
-                // the blocks of steps t and t + 1 at once and swap them
-                const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)(t + (i & 1)));
-                uint32_t o[4];
+                ux = k.k_si * (gx - px);
+                uy = k.k_si * (gy - py);
+                cap_fast(ux, uy, k.vmax);
+                uint32_t wx, wy;
+                if (nz_ep == ep && nz_t + 1 == t) {
+                    wx = nz_nx;
+                    wy = nz_ny;
+                    nz_t = -2;
+                } else {
+                    // robots 2m and 2m + 1 share the Philox block (pair m, step t): their lanes draw
+                    // the blocks of steps t and t + 1 at once and swap them
+                    const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)(t + (i & 1)));
+                    uint32_t o[4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) o[m] = __shfl_xor_sync(tm.mask, w.w[m], 1, 4);
-                wx = (i & 1) ? o[2] : w.w[0];
-                wy = (i & 1) ? o[3] : w.w[1];
-                nz_nx = (i & 1) ? w.w[2] : o[0];
-                nz_ny = (i & 1) ? w.w[3] : o[1];
-                nz_t = t;
-                nz_ep = ep;
-            }
-            {
-                const float ex = __fmul_rn(__fsub_rn(unit24(wx), 0.5f), k.noise_scale);
-                const float ey = __fmul_rn(__fsub_rn(unit24(wy), 0.5f), k.noise_scale);
-                ux += k.noise_on ? ex : 0.f;
-                uy += k.noise_on ? ey : 0.f;
+                    for (int m = 0; m < 4; ++m) o[m] = __shfl_xor_sync(tm.mask, w.w[m], 1, 4);
+                    wx = (i & 1) ? o[2] : w.w[0];
+                    wy = (i & 1) ? o[3] : w.w[1];
+                    nz_nx = (i & 1) ? w.w[2] : o[0];
+                    nz_ny = (i & 1) ? w.w[3] : o[1];
+                    nz_t = t;
+                    nz_ep = ep;
+                }
+                {
+                    const float ex = __fmul_rn(__fsub_rn(unit24(wx), 0.5f), k.noise_scale);
+                    const float ey = __fmul_rn(__fsub_rn(unit24(wy), 0.5f), k.noise_scale);
+                    ux += k.noise_on ? ex : 0.f;
+                    uy += k.noise_on ? ey : 0.f;
+                }
             }
             cap_fast(ux, uy, k.vmax);
             const float dold = fast_norm(px - gx, py - gy);

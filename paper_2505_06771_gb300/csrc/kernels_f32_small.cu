@@ -23,7 +23,13 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
     const bool fast = is_fast(a);
     int variant = a.variant;
     if (fast && a.k.controller != 0) variant = 2;  // the pose controller: gather kernel only
-    if (fast && variant == 3 && a.warp_envs <= 0 && max_blocks <= 0) {
+    // policy actions without traces (the policy-in-the-loop step): the split kernel, whose
+    // dynamics take the actions as nominal velocities
+    const bool split_ok = fast || (a.k.scenario == 0 && a.k.controller == 0 && a.io.u_nom == nullptr &&
+                                   a.io.u_star == nullptr && a.io.vw == nullptr &&
+                                   a.io.qp_info == nullptr);
+    if (!fast && split_ok && variant == 0) variant = 3;
+    if (split_ok && variant == 3 && a.warp_envs <= 0 && max_blocks <= 0) {
         // dynamics and output warps (env_split.cuh): one block of 4 + 4 warps per SM, the envs
         // spread evenly over the dynamics warps when that leaves at most 8 per warp
         int dev = 0, sms = 0;

@@ -84,7 +84,8 @@ def test_reset_sampler_bit_exact(rl, prec, case):
 
 def _teacher_forced(rl, g, o, n, seed, steps, actions=False, traces=True):
     """Both sides step from the same state.  traces=False calls the step with observations,
-    rewards and done flags only, which selects the one-thread-per-env Navigation kernel."""
+    rewards and done flags only, which selects the kernels that write no traces (the 4-robot
+    Navigation fast paths the configuration names)."""
     env = rl.Env(g, len(n), n, seed)
     b = _alloc(env)
     if not traces:
@@ -236,6 +237,18 @@ def test_teacher_forced_fast_kernels(rl, kern, N, E):
     g, o = make_pair(0, N, episode_len=30, **FAST_KERNELS[kern])
     err, _ = _teacher_forced(rl, g, o, [N] * E, 91, 40, traces=False)
     print(f"\n{kern} kernel N={N}: max errors {err}")
+    assert err["pose"] < POSE_STEP_TOL and err["th"] < 2e-5
+    assert err["rew"] < 1e-5 and err["obs"] < 1e-5
+
+
+@pytest.mark.parametrize("N,E", [(4, 600), (3, 300), (4, 1)])
+def test_teacher_forced_policy_actions_split_kernel(rl, N, E):
+    """Policy actions without traces (the policy-in-the-loop step) run the split kernel, its
+    dynamics taking the actions as nominal velocities: poses, observations and rewards against
+    the oracle stepped from the same state with the same actions."""
+    g, o = make_pair(0, N, scripted=0, episode_len=30)
+    err, _ = _teacher_forced(rl, g, o, [N] * E, 63, 35, actions=True, traces=False)
+    print(f"\nsplit kernel, policy actions, N={N} E={E}: max errors {err}")
     assert err["pose"] < POSE_STEP_TOL and err["th"] < 2e-5
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
