@@ -13,6 +13,7 @@
 #pragma once
 #include "env_step.cuh"
 #include "qp_regs.cuh"
+#include "qp_team.cuh"
 #include "qp_warp.cuh"
 
 namespace rl {
@@ -382,12 +383,12 @@ __device__ __forceinline__ QPResult small_filter(const Team<4>& tm, TeamSmem<flo
 
 // The barrier QP of one env of N <= 4 robots, solved redundantly by every lane of the team.
 // One round of shuffles all-gathers the projected points and nominal velocities; then each lane
-// runs the register dual active-set solver (thread_qp: 22 row slots in tie-break order,
-// closed-form first iteration) on the whole 8-variable QP, with no cross-lane traffic inside
-// the solve, and keeps its own robot's u.  Every lane takes the same branches, so the team
-// never diverges; an active set beyond kRegRows rows goes to the shared-memory solver.
-// defer: an active set beyond kRegRows rows is not solved here but returned as status 3 (the
-// caller hands it to the whole warp).
+// runs the register dual active-set solver (team_qp: pair rows first, then the arena rows
+// checked once; closed-form first iteration) on the whole 8-variable QP, with no cross-lane
+// traffic inside the solve, and keeps its own robot's u.  Every lane takes the same branches,
+// so the team never diverges; an active set beyond kTeamRows rows goes to the shared-memory
+// solver.  defer: an active set beyond kTeamRows rows is not solved here but returned as
+// status 3 (the caller hands it to the whole warp).
 __device__ __forceinline__ QPResult small_filter_all(const Team<4>& tm, TeamSmem<float, 4>& S,
                                                      int N, float px, float py, float u0x,
                                                      float u0y, const QPConsts<float>& c,
@@ -401,7 +402,7 @@ __device__ __forceinline__ QPResult small_filter_all(const Team<4>& tm, TeamSmem
         U0[2 * j + 1] = __shfl_sync(tm.mask, u0y, j, 4);
     }
     bool overflow;
-    QPResult res = thread_qp<float, kRegRows>(Px, Py, N, U0, c, U, overflow);
+    QPResult res = team_qp<kTeamRows>(Px, Py, N, U0, c, U, overflow);
     if (overflow && defer) {
         res.status = 3;
         usx = u0x;

@@ -119,7 +119,7 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
             cap_fast(ux, uy, k.vmax);
             const float dold = fast_norm(px - gx, py - gy);
 
-            // ---- the barrier QP: every lane solves the team's QP in registers (at most four
+            // ---- the barrier QP: every lane solves the team's QP in registers (at most six
             // active rows); a larger active set, and the binary64 re-solve of a flagged QP, by
             // the warp's live lanes (or by the team when it is alone in its warp)
             float usx, usy;

@@ -6,8 +6,9 @@
 // CAP active rows with their multipliers and Cholesky factor.  The dual active-set iteration is
 // the one of qp_solve in env_step.cuh (Goldfarb-Idnani on H = I, Sec. 3 barrier QP); its first
 // step, the projection onto the most violated row's half-plane, is closed form.
-// Used by the one-thread-per-env kernel (env_thread.cuh) and, redundantly in every lane of a
-// 4-lane team, by the register team kernel (env_small.cuh).
+// Used by the one-thread-per-env kernel (env_thread.cuh) and by the gather team kernel's second
+// violated row (env_nav4.cuh); the register team kernels use team_qp (qp_team.cuh), the same
+// iteration with the pair rows taken first.
 #pragma once
 #include "env_step.cuh"
 
