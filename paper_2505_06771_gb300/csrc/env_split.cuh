@@ -14,6 +14,19 @@
 // (bar.arrive by the writer, bar.sync by the reader, one pair per warp pair), so the handover
 // costs the dynamics warp one barrier arrival and two shared stores per step.
 //
+// The output warp also takes two state-independent pieces of the step off the dynamics warp:
+//  * the action noise: after reading step s it draws the Philox words of step s + 3 into a
+//    ring of four steps that the dynamics warp reads (steps 0-2 of a launch are drawn by the
+//    dynamics warp itself);
+//  * the auto-reset sample: after reading the step that began an episode (or before its first
+//    step, for the launch's first episode) it samples the next episode's initial poses, goals
+//    and levels into its own team record, which the dynamics warp reads at the episode's end.
+// Both are read at least three steps after they were written; the barriers of the two steps in
+// between order the accesses (the writer has passed them only after finishing the write, the
+// reader waits on them), and a slot is rewritten only after the reader has arrived past its
+// read.  An episode end closer than that (episodes shorter than three steps, or the first one
+// ending before step 2) is sampled by the dynamics warp as before.
+//
 // Both warps of a pair run the same T steps over the same envs, every lane of both warps
 // executing every barrier (teams without an env skip only the work), so every barrier completes.
 #pragma once
@@ -26,7 +39,15 @@ struct SplitSlot {
     float4 r[8][4][2];  // [team][robot]: (npx, npy, reward term, gy), (x, y, th, gx)
     int done[8];        // [team]: the episode ended (the pose above is the new episode's)
     int oob[8];         // [team]: robots whose projected point left the arena this step
+    uint2 noise[4][8][4];  // [step & 3][team][robot]: Philox words of the robot's action noise
 };
+
+// Noise words of robot i for step t of episode ep (robots 2m and 2m + 1 share the block of
+// pair m, as in the other 4-robot kernels).
+__device__ __forceinline__ uint2 split_noise(uint64_t seed, int e, int ep, int i, int t) {
+    const Words4 w = draw(seed, e, ep, kNoise, i >> 1, (uint32_t)t);
+    return (i & 1) ? make_uint2(w.w[2], w.w[3]) : make_uint2(w.w[0], w.w[1]);
+}
 
 // Named barriers of warp pair p (ids 1..8; id 0 is left to __syncthreads).  Both warps count:
 // 64 threads.
@@ -42,7 +63,8 @@ __device__ __forceinline__ int split_empty_id(int p) { return 2 + 2 * p; }
 // The dynamics warp of a pair: live teams step their env T times; every lane executes the
 // handover of every step.
 static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A, const Team<4>& tm,
-                                                      TeamSmem<float, 4>& S, SplitSlot& slot,
+                                                      TeamSmem<float, 4>& S,
+                                                      const TeamSmem<float, 4>& So, SplitSlot& slot,
                                                       int p, int tiw, int e, unsigned wm) {
     const StepConsts<float>& k = A.k;
     const bool live = e >= 0;
@@ -71,8 +93,7 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
     float sn, cs;
     __sincosf(th, &sn, &cs);
     int c_succ = 0, c_act = 0, c_flag = 0, c_inf = 0, c_ep = 0, c_it = 0;
-    int nz_t = -2, nz_ep = -1;  // noise words cached for step nz_t + 1 of episode nz_ep
-    uint32_t nz_nx = 0u, nz_ny = 0u;
+    int last_reset = -1;  // the step of the last episode end (-1: none in this launch)
 
     for (int step = 0; step < A.T; ++step) {
         float npx = 0.f, npy = 0.f, dterm = 0.f;
@@ -90,28 +111,12 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
                 ux = k.k_si * (gx - px);
                 uy = k.k_si * (gy - py);
                 cap_fast(ux, uy, k.vmax);
-                uint32_t wx, wy;
-                if (nz_ep == ep && nz_t + 1 == t) {
-                    wx = nz_nx;
-                    wy = nz_ny;
-                    nz_t = -2;
-                } else {
-                    // robots 2m and 2m + 1 share the Philox block (pair m, step t): their lanes draw
-                    // the blocks of steps t and t + 1 at once and swap them
-                    const Words4 w = draw(A.seed, e, ep, kNoise, i >> 1, (uint32_t)(t + (i & 1)));
-                    uint32_t o[4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) o[m] = __shfl_xor_sync(tm.mask, w.w[m], 1, 4);
-                    wx = (i & 1) ? o[2] : w.w[0];
-                    wy = (i & 1) ? o[3] : w.w[1];
-                    nz_nx = (i & 1) ? w.w[2] : o[0];
-                    nz_ny = (i & 1) ? w.w[3] : o[1];
-                    nz_t = t;
-                    nz_ep = ep;
-                }
+                // the noise words: from the output warp's ring from step 3 on
+                const uint2 w = step >= 3 ? slot.noise[step & 3][tiw][i]
+                                          : split_noise(A.seed, e, ep, i, t);
                 {
-                    const float ex = __fmul_rn(__fsub_rn(unit24(wx), 0.5f), k.noise_scale);
-                    const float ey = __fmul_rn(__fsub_rn(unit24(wy), 0.5f), k.noise_scale);
+                    const float ex = __fmul_rn(__fsub_rn(unit24(w.x), 0.5f), k.noise_scale);
+                    const float ey = __fmul_rn(__fsub_rn(unit24(w.y), 0.5f), k.noise_scale);
                     ux += k.noise_on ? ex : 0.f;
                     uy += k.noise_on ? ey : 0.f;
                 }
@@ -244,12 +249,21 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
                 c_ep += 1;
                 ep += 1;
                 t = 0;
-                small_reset(tm, S, A, e, ep, N);
-                if (own) {
-                    x = S.fx[i]; y = S.fy[i]; th = S.fth[i];
-                    gx = S.sx[i]; gy = S.sy[i]; gth = S.sth[i]; lv = S.slevel[i];
+                if (step >= last_reset + 3) {
+                    // sampled ahead by the output warp
+                    if (own) {
+                        x = So.fx[i]; y = So.fy[i]; th = So.fth[i];
+                        gx = So.sx[i]; gy = So.sy[i]; gth = So.sth[i]; lv = So.slevel[i];
+                    }
+                } else {
+                    small_reset(tm, S, A, e, ep, N);
+                    if (own) {
+                        x = S.fx[i]; y = S.fy[i]; th = S.fth[i];
+                        gx = S.sx[i]; gy = S.sy[i]; gth = S.sth[i]; lv = S.slevel[i];
+                    }
+                    tm.sync();
                 }
-                tm.sync();
+                last_reset = step;
                 __sincosf(th, &sn, &cs);
             }
         }
@@ -285,7 +299,8 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
 // The output warp of a pair: per step, the flags, the team reward, the observations and the
 // reward and done streams of the pair's envs, from the dynamics warp's slot.
 static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A, const Team<4>& tm,
-                                                     const SplitSlot& slot, int p, int tiw, int e) {
+                                                     TeamSmem<float, 4>& So, SplitSlot& slot,
+                                                     int p, int tiw, int e) {
     const StepConsts<float>& k = A.k;
     const bool live = e >= 0;
     const int N = live ? A.s.nrob[e] : 0;
@@ -298,6 +313,10 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
     int c_col = 0, c_oob = 0;
     float ret_acc = 0.f;
     const int od = A.io.obs_dim;
+    const bool scripted = A.io.actions == nullptr;
+    // the env's episode clock (the dynamics warp's, advanced by the published done flags)
+    int t = live ? A.s.t[e] : 0, ep = live ? A.s.ep[e] : 0;
+    if (live) small_reset(tm, So, A, e, ep + 1, N);  // the launch's first episode end
 
     for (int step = 0; step < A.T; ++step) {
         __syncwarp();
@@ -312,6 +331,16 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
         const int oob = slot.oob[tiw];
         split_arrive(split_empty_id(p));
         if (!live) continue;
+        // the episode clock at the start of step + 1, then the noise of step + 3 and, after an
+        // episode end, the next episode's initial state
+        if (done) { t = 0; ++ep; } else { ++t; }
+        if (scripted) {
+            int t3 = t + 1, ep3 = ep;
+            if (t3 >= k.episode_len) { t3 = 0; ++ep3; }
+            if (++t3 >= k.episode_len) { t3 = 0; ++ep3; }
+            if (own) slot.noise[(step + 3) & 3][tiw][i] = split_noise(A.seed, e, ep3, i, t3);
+        }
+        if (done) small_reset(tm, So, A, e, ep + 1, N);
         // collisions of the projected points after the Euler step (before any reset), the
         // team reward
         int col = 0;
@@ -395,11 +424,13 @@ __global__ void __launch_bounds__(256, 1) env_kernel_split(LaunchArgs<float> A) 
     const int e = idx < hi ? (A.env_list ? A.env_list[idx] : A.env_begin + idx) : -1;
     if (warp_in_block < 4) {
         TeamSmem<float, 4>* S = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + (threadIdx.x >> 2);
+        const TeamSmem<float, 4>* So = S + 32;  // the partner output team's record
         const int nw = hi - lo;  // the warp's live teams, for the warp-wide rare QPs
         const unsigned wm = nw >= 8 ? 0xffffffffu : (nw >= 2 ? (1u << (4 * nw)) - 1u : 0u);
-        split_dynamics(A, tm, *S, slots[p], p, tiw, e, wm);
+        split_dynamics(A, tm, *S, *So, slots[p], p, tiw, e, wm);
     } else {
-        split_outputs(A, tm, slots[p], p, tiw, e);
+        TeamSmem<float, 4>* So = reinterpret_cast<TeamSmem<float, 4>*>(smem_raw) + (threadIdx.x >> 2);
+        split_outputs(A, tm, *So, slots[p], p, tiw, e);
     }
 }
 

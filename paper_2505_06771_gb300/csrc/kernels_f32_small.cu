@@ -38,7 +38,7 @@ static cudaError_t launch_small_regs(const LaunchArgs<float>& a, int block_threa
         if (e != cudaSuccess) return e;
         const int blocks = std::min(sms, (a.n_list + 3) / 4);
         if (blocks >= 1 && a.n_list <= 8 * 4 * blocks) {
-            const size_t sp = (size_t)32 * sizeof(TeamSmem<float, 4>);
+            const size_t sp = (size_t)64 * sizeof(TeamSmem<float, 4>);  // dynamics + output teams
             e = cudaFuncSetAttribute(env_kernel_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sp);
             if (e != cudaSuccess) return e;

@@ -24,6 +24,11 @@
 namespace rl {
 
 constexpr int kTeamRows = 6;
+// Quotients, square roots and their reciprocals here are the hardware approximations
+// (__fdividef, rsqrtf: about 2 ulp), not the correctly rounded ones: they only scale steps and
+// factors, so their error stays at binary32 rounding level in the minimiser.  A divisor must be
+// above kTinyPos (a multiplier ratio with a smaller positive divisor is an unbounded step).
+constexpr float kTinyPos = 1e-30f;
 
 // Bound of arena side s (0 +x, 1 -x, 2 +y, 3 -y) of a robot at projected point (px, py).
 template <typename Q>
@@ -152,15 +157,15 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
         Q a[8], b, h;
         team_row(R, r, a, b, h, c.r2);
         const Q app = tdot(a, a);
-        const Q st = vb / app;
+        const Q st = __fdividef(vb, app);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             U[m] -= st * a[m];
             AR[0][m] = a[m];
         }
         lam[0] = st;
-        L[0] = sqrtf(app);
-        dinv[0] = (Q)1 / L[0];
+        dinv[0] = rsqrtf(app);
+        L[0] = app * dinv[0];
         hlow = (h < c.h_flag) ? 1u : 0u;
         slots = (unsigned)r;
         act = 1u << r;
@@ -186,8 +191,8 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
 #pragma unroll
                 for (int m = 0; m < 8; ++m) z[m] = ap[m] - r0 * AR[0][m];
                 const Q zz = tdot(z, z);
-                const Q td = r0 > (Q)0 ? lam[0] / r0 : CUDART_INF_F;
-                const Q tf = (tdot(ap, U) - bp) / zz;
+                const Q td = r0 > kTinyPos ? __fdividef(lam[0], r0) : CUDART_INF_F;
+                const Q tf = __fdividef(tdot(ap, U) - bp, zz);
                 if (zz > c.eps_dep * app && tf <= td) {
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
@@ -195,10 +200,9 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
                         AR[1][m] = ap[m];
                     }
                     lam[0] -= tf * r0;
-                    const Q dg = sqrtf(zz);
+                    dinv[1] = rsqrtf(zz);
                     L[1] = y0;
-                    L[2] = dg;
-                    dinv[1] = (Q)1 / dg;
+                    L[2] = zz * dinv[1];
                     lam[1] = tf;
                     hlow |= (hp < c.h_flag) ? 2u : 0u;
                     slots |= (unsigned)r << 5;
@@ -244,14 +248,14 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
                 int jb = -1;
 #pragma unroll
                 for (int t = 0; t < CAP; ++t)
-                    if (t < q && rr[t] > (Q)0) {
-                        const Q tj = lam[t] / rr[t];
+                    if (t < q && rr[t] > kTinyPos) {
+                        const Q tj = __fdividef(lam[t], rr[t]);
                         if (tj < td) { td = tj; jb = t; }
                     }
                 const Q sp = tdot(ap, U) - bp;
                 const bool indep = zz > c.eps_dep * app;
                 if (!indep) res.flag = true;
-                const Q tf = indep ? sp / zz : CUDART_INF_F;
+                const Q tf = indep ? __fdividef(sp, zz) : CUDART_INF_F;
                 if (!(tf < CUDART_INF_F) && !(td < CUDART_INF_F)) {
                     res.status = 1;
                     break;
@@ -267,14 +271,14 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
                 lam_p += st;
                 if (tf <= td) {
                     if (q == CAP) { overflow = true; break; }
-                    const Q dg = sqrtf(zz);
+                    const Q di = rsqrtf(zz);
 #pragma unroll
                     for (int t = 0; t < CAP; ++t) {
                         if (t == q) {
 #pragma unroll
                             for (int m = 0; m < t; ++m) L[ttri(t, m)] = y[m];
-                            L[ttri(t, t)] = dg;
-                            dinv[t] = (Q)1 / dg;
+                            L[ttri(t, t)] = zz * di;
+                            dinv[t] = di;
 #pragma unroll
                             for (int m = 0; m < 8; ++m) AR[t][m] = ap[m];
                             lam[t] = lam_p;
@@ -312,9 +316,9 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
                                 for (int n = 0; n < m; ++n) g -= L[ttri(t, n)] * L[ttri(m, n)];
                                 if (m == t) {
                                     ok = ok && (g > (Q)0);
-                                    const Q dg = sqrtf(g > (Q)1e-30 ? g : (Q)1e-30);
-                                    L[ttri(t, t)] = dg;
-                                    dinv[t] = (Q)1 / dg;
+                                    const Q gp = g > (Q)1e-30 ? g : (Q)1e-30;
+                                    dinv[t] = rsqrtf(gp);
+                                    L[ttri(t, t)] = gp * dinv[t];
                                 } else {
                                     L[ttri(t, m)] = g * dinv[m];
                                 }

@@ -486,6 +486,34 @@ def test_split_rollout_equals_steps_crowded(rl):
     b.close()
 
 
+@pytest.mark.parametrize("episode_len", [1, 2, 3, 4, 7])
+def test_split_rollout_equals_steps_episode_ends(rl, episode_len):
+    """The split kernel's output warps draw the action noise three steps ahead and sample each
+    next episode's start ahead of its end; the dynamics warps draw and sample themselves where
+    that is too close (the first three steps of a launch, episodes shorter than three steps, a
+    first episode end before step 2).  Launches of 29 steps started mid-episode give the same
+    trajectories and state as 29 one-step launches (which take only the dynamics warps' own
+    draws), bit for bit, for episode lengths around that limit."""
+    g, _ = make_pair(0, 4, episode_len=episode_len, small_variant=3)
+    n, T = [4] * 300 + [3] * 40 + [2] * 17, 29
+    E = len(n)
+    a = rl.Env(g, E, n, 31)
+    a.rollout(5)
+    b = rl.Env(g, E, n, 31)
+    b.set_state(a.get_state())
+    bt = _alloc(a, T)
+    a.rollout(T, **bt)
+    for t in range(T):
+        bs = _alloc(b)
+        b.step(obs=bs["obs"], reward=bs["reward"], done=bs["done"])
+        assert torch.equal(bs["obs"], bt["obs"][t]) and torch.equal(bs["reward"], bt["reward"][t])
+        assert torch.equal(bs["done"], bt["done"][t])
+    assert int(bt["done"].sum()) > 0
+    assert a.get_state() == b.get_state()
+    a.close()
+    b.close()
+
+
 def test_uneven_classes_in_one_batch(rl):
     """Envs of 2..32 robots (every size class, ragged class sizes) in one handle."""
     n = [2, 3, 4, 5, 7, 8, 9, 12, 16, 17, 25, 32] * 5
