@@ -38,7 +38,6 @@ namespace rl {
 struct SplitSlot {
     float4 r[8][4][2];  // [team][robot]: (npx, npy, reward term, gy), (x, y, th, gx)
     int done[8];        // [team]: the episode ended (the pose above is the new episode's)
-    int oob[8];         // [team]: robots whose projected point left the arena this step
     uint2 noise[4][8][4];  // [step & 3][team][robot]: Philox words of the robot's action noise
 };
 
@@ -97,7 +96,7 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
 
     for (int step = 0; step < A.T; ++step) {
         float npx = 0.f, npy = 0.f, dterm = 0.f;
-        int done = 0, oob_i = 0;
+        int done = 0;
         if (live) {
             // ---- projected point and nominal SI velocity: the policy's action, or go to goal,
             // cap, noise; then the cap
@@ -226,7 +225,6 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
             npx = x + k.l * cs;
             npy = y + k.l * sn;
             dterm = own ? dold - fast_norm(npx - gx, npy - gy) : 0.f;
-            oob_i = (own && (npx < k.xmin || npx > k.xmax || npy < k.ymin || npy > k.ymax)) ? 1 : 0;
             if (k.waypoint && own) {
                 const float ex = npx - gx, ey = npy - gy;
                 if (ex * ex + ey * ey < k.goal_eps2) {
@@ -272,11 +270,7 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
         if (step > 0) split_wait(split_empty_id(p));
         slot.r[tiw][i][0] = make_float4(npx, npy, dterm, gy);
         slot.r[tiw][i][1] = make_float4(x, y, th, gx);
-        const int oob = __reduce_add_sync(0xffffffffu, oob_i << (4 * tiw));  // 4 bits per team
-        if (i == 0) {
-            slot.done[tiw] = done;
-            slot.oob[tiw] = (oob >> (4 * tiw)) & 15;
-        }
+        if (i == 0) slot.done[tiw] = done;
         split_arrive(split_full_id(p));
     }
     if (A.T > 0) split_wait(split_empty_id(p));
@@ -328,7 +322,6 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
             b[r] = slot.r[tiw][r][1];
         }
         const int done = slot.done[tiw];
-        const int oob = slot.oob[tiw];
         split_arrive(split_empty_id(p));
         if (!live) continue;
         // the episode clock at the start of step + 1, then the noise of step + 3 and, after an
@@ -341,13 +334,17 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
             if (own) slot.noise[(step + 3) & 3][tiw][i] = split_noise(A.seed, e, ep3, i, t3);
         }
         if (done) small_reset(tm, So, A, e, ep + 1, N);
-        // collisions of the projected points after the Euler step (before any reset), the
-        // team reward
-        int col = 0;
+        // collisions and arena exits of the projected points after the Euler step (before any
+        // reset), the team reward
+        int col = 0, oob = 0;
         float rew = 0.f;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-            if (r < N) rew += a[r].z;
+            if (r < N) {
+                rew += a[r].z;
+                oob += (a[r].x < k.xmin || a[r].x > k.xmax || a[r].y < k.ymin || a[r].y > k.ymax)
+                           ? 1 : 0;
+            }
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll

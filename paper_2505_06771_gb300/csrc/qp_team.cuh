@@ -83,6 +83,20 @@ __device__ __forceinline__ int arena_scan(const Q (&bb)[16], const Q (&U)[8], un
     return i0;
 }
 
+// Whether any valid arena row is violated at u (the check of the common path: no argmax).
+template <typename Q>
+__device__ __forceinline__ bool arena_any(const Q (&bb)[16], const Q (&U)[8], int N,
+                                          const QPConsts<Q>& c) {
+    bool v = false;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int i = m >> 2, s = m & 3;
+        const Q au = (s == 0) ? U[2 * i] : (s == 1) ? -U[2 * i] : (s == 2) ? U[2 * i + 1] : -U[2 * i + 1];
+        v |= (i < N) & (au - bb[m] > c.tol_abs + c.tol_rel * fabs(bb[m]));
+    }
+    return v;
+}
+
 // Dense coefficients, bound and h (arena rows: +inf) of slot r: a pair row from the cached
 // differences, an arena row from its bound.
 template <typename Q>
@@ -339,6 +353,7 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
         all_rows = true;
 #pragma unroll
         for (int m = 0; m < 16; ++m) R.bb[m] = arena_bound(c, m & 3, Px[m >> 2], Py[m >> 2]);
+        if (!arena_any(R.bb, U, N, c)) break;
         vb = (Q)0;
         r = arena_scan(R.bb, U, act, N, c, vb, -1);
         if (r < 0) break;
