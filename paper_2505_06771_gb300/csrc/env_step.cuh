@@ -181,22 +181,40 @@ struct QPWork {
     int fail;
 };
 
-// Explicit-inverse workspace of the binary32 solver qp_solve_inv (see there).
-template <int NMAX>
+// Explicit-inverse workspace of qp_solve_inv (see there): Q the precision, AS the slots (the
+// most active rows it holds; 2 NMAX, the variables, in binary32).
+template <int NMAX, typename Q = float, int AS = 2 * NMAX>
 struct InvWork {
-    static constexpr int A = 2 * NMAX;                          // slots (active rows at most)
+    static constexpr int A = AS;                                // slots (active rows at most)
     static constexpr int V = 2 * NMAX;                          // variables
+    static_assert(AS <= 64, "free slots are a 64-bit mask");
     // rows padded to A + 1 words: lanes walking their own rows hit distinct banks
-    float Mi[V][A + 1];      // M = N G^-1, variable x slot
-    float Bi[A][A + 1];      // B = G^-1, slot x slot
-    float r[A];
-    float lam[A], sax[A], say[A], sb[A];
+    Q Mi[V][A + 1];          // M = N G^-1, variable x slot
+    Q Bi[A][A + 1];          // B = G^-1, slot x slot
+    Q r[A];
+    Q lam[A], sax[A], say[A], sb[A];
     int sia[A], sib[A], sk[A];
     int act[A];              // active slots in order of addition
+    Q zx[NMAX], zy[NMAX];                // z = a_p - N r per robot (for the factor updates)
+    unsigned long long inc[NMAX];        // per robot: the active slots whose row touches it
     unsigned long long free_slots;
 };
 
 struct NoInvWork {};
+
+// Slots of the binary64 explicit-inverse re-solve: enough for the active sets met (a QP that
+// needs more falls back to the Cholesky form) while its workspace stays within the binary32
+// one, so that the union below does not grow.
+template <int NMAX>
+constexpr int f64_inv_slots() { return NMAX <= 8 ? 2 * NMAX : (NMAX <= 20 ? 24 : 32); }
+
+// binary64 explicit-inverse re-solve work: the QP data the solver reads (points, u) and its
+// factors.
+template <int NMAX>
+struct F64Inv {
+    double px[NMAX], py[NMAX], ux[NMAX], uy[NMAX], u0x[NMAX], u0y[NMAX];
+    InvWork<NMAX, double, f64_inv_slots<NMAX>()> inv;
+};
 
 // binary32 work (the QP data and, for teams over 4 robots, the explicit-inverse factors)
 // overlays the binary64 re-solve work: the re-solve starts after the binary32 result is read.
@@ -210,6 +228,7 @@ template <int NMAX>
 union QPUnion {
     F32Work<NMAX> s;
     QPWork<double, NMAX> d;
+    typename std::conditional<(NMAX > 4), F64Inv<NMAX>, NoInvWork>::type di;
 };
 
 template <typename R, int NMAX>
@@ -655,41 +674,41 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
 // circulant pair rows (partner, p_a - p_b, bound, key) and its four arena rows, computed once per
 // QP; "on" marks the ones currently in the active set.  key = row index * 32 + lane, so that an
 // argmax over keys breaks ties by row index and names the lane holding the row.
-template <int NMAX>
+template <int NMAX, typename Q = float>
 struct LaneRows {
     static constexpr int PR = NMAX / 2 > 0 ? NMAX / 2 : 1;
-    float dx[PR], dy[PR], bp[PR];
+    Q dx[PR], dy[PR], bp[PR];
     int j[PR], key[PR];
-    float bb[4];
+    Q bb[4];
     int bkey[4];
     int np;
     unsigned on;  // bit d: pair row d active; bit PR + s: arena row s active
 };
 
-template <int NMAX>
-__device__ __forceinline__ void lane_rows_init(LaneRows<NMAX>& R, int i, int N, const float* px,
-                                               const float* py, const QPConsts<float>& c) {
+template <int NMAX, typename Q>
+__device__ __forceinline__ void lane_rows_init(LaneRows<NMAX, Q>& R, int i, int N, const Q* px,
+                                               const Q* py, const QPConsts<Q>& c) {
     const int nd = (N - 1) / 2;
     R.np = (i < N) ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
     R.on = 0u;
     const int P = N * (N - 1) / 2;
 #pragma unroll
-    for (int d = 0; d < LaneRows<NMAX>::PR; ++d) {
+    for (int d = 0; d < LaneRows<NMAX, Q>::PR; ++d) {
         int j = i + d + 1;
         while (j >= N) j -= N;
         if (d >= R.np) j = i;
         const int a = min(i, j), b = max(i, j);
-        const float sg = (a == i) ? 1.f : -1.f;
+        const Q sg = (a == i) ? (Q)1 : (Q)-1;
         R.j[d] = j;
         R.key[d] = (d < R.np) ? pair_index(a, b, N) * 32 + (i & 31) : 0x7fffffff;
         R.dx[d] = sg * (px[i < N ? i : 0] - px[j < N ? j : 0]);
         R.dy[d] = sg * (py[i < N ? i : 0] - py[j < N ? j : 0]);
-        const float h = R.dx[d] * R.dx[d] + R.dy[d] * R.dy[d] - c.r2;
+        const Q h = R.dx[d] * R.dx[d] + R.dy[d] * R.dy[d] - c.r2;
         R.bp[d] = c.gamma * h * h * h;
     }
-    const float pxi = px[i < N ? i : 0], pyi = py[i < N ? i : 0];
-    const float bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
-    const float by0 = c.ymax - c.half_r - pyi, by1 = pyi - c.ymin - c.half_r;
+    const Q pxi = px[i < N ? i : 0], pyi = py[i < N ? i : 0];
+    const Q bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
+    const Q by0 = c.ymax - c.half_r - pyi, by1 = pyi - c.ymin - c.half_r;
     R.bb[0] = c.kg * bx0 * bx0 * bx0;
     R.bb[1] = c.kg * bx1 * bx1 * bx1;
     R.bb[2] = c.kg * by0 * by0 * by0;
@@ -700,24 +719,23 @@ __device__ __forceinline__ void lane_rows_init(LaneRows<NMAX>& R, int i, int N, 
 
 // Most violated inactive row of the team at u (shared memory), its descriptor broadcast from
 // the lane that holds it.  Returns false when every row holds.
-template <int G, int NMAX>
-__device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NMAX>& R, int i,
-                                            const float* ux, const float* uy,
-                                            const QPConsts<float>& c, RowInfo<float>& p,
-                                            float& vbest) {
-    float vb = 0.f;
+template <typename Q, int G, int NMAX>
+__device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NMAX, Q>& R, int i,
+                                            const Q* ux, const Q* uy, const QPConsts<Q>& c,
+                                            RowInfo<Q>& p, Q& vbest) {
+    Q vb = (Q)0;
     int kb = 0x7fffffff, ba = -1, bbv = -1;
-    float bdx = 0.f, bdy = 0.f, bbound = 0.f;
+    Q bdx = (Q)0, bdy = (Q)0, bbound = (Q)0;
     if (R.np > 0 || (R.bkey[0] != 0x7fffffff)) {
-        const float uxi = ux[i], uyi = uy[i];
+        const Q uxi = ux[i], uyi = uy[i];
 #pragma unroll
-        for (int d = 0; d < LaneRows<NMAX>::PR; ++d) {
+        for (int d = 0; d < LaneRows<NMAX, Q>::PR; ++d) {
             if (d < R.np && !((R.on >> d) & 1u)) {
                 const int j = R.j[d];
-                const float sg = (i < j) ? 1.f : -1.f;
-                const float dux = sg * (uxi - ux[j]), duy = sg * (uyi - uy[j]);
-                const float v = -2.f * (R.dx[d] * dux + R.dy[d] * duy) - R.bp[d];
-                if (v > c.tol_abs + c.tol_rel * fabsf(R.bp[d]) &&
+                const Q sg = (i < j) ? (Q)1 : (Q)-1;
+                const Q dux = sg * (uxi - ux[j]), duy = sg * (uyi - uy[j]);
+                const Q v = (Q)-2 * (R.dx[d] * dux + R.dy[d] * duy) - R.bp[d];
+                if (v > c.tol_abs + c.tol_rel * fabs(R.bp[d]) &&
                     (v > vb || (v == vb && R.key[d] < kb))) {
                     vb = v;
                     kb = R.key[d];
@@ -729,12 +747,12 @@ __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NM
                 }
             }
         }
-        const float aus[4] = {uxi, -uxi, uyi, -uyi};
+        const Q aus[4] = {uxi, -uxi, uyi, -uyi};
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            const float v = aus[s] - R.bb[s];
-            if (R.bkey[s] != 0x7fffffff && !((R.on >> (LaneRows<NMAX>::PR + s)) & 1u) &&
-                v > c.tol_abs + c.tol_rel * fabsf(R.bb[s]) &&
+            const Q v = aus[s] - R.bb[s];
+            if (R.bkey[s] != 0x7fffffff && !((R.on >> (LaneRows<NMAX, Q>::PR + s)) & 1u) &&
+                v > c.tol_abs + c.tol_rel * fabs(R.bb[s]) &&
                 (v > vb || (v == vb && R.bkey[s] < kb))) {
                 vb = v;
                 kb = R.bkey[s];
@@ -744,48 +762,76 @@ __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NM
             }
         }
     }
-    tm.argmax(vb, kb);
-    vbest = vb;
-    if (kb == 0x7fffffff) return false;
-    const int own = kb & 31 & (G - 1);
+    // the team's largest violation (non-negative floats order as their bits; a binary64 one is
+    // compared rounded to binary32, which only orders the iterations), held by the lowest lane
+    // that has it
+    const unsigned vbits = __float_as_uint((float)vb);
+    const unsigned vmax = __reduce_max_sync(tm.mask, vbits);
+    if (vmax == 0u) return false;
+    const int own = (__ffs(__ballot_sync(tm.mask, vbits == vmax)) - 1) & (G - 1);
+    vbest = __shfl_sync(tm.mask, vb, own, G);
+    kb = __shfl_sync(tm.mask, kb, own, G);
     const int a = __shfl_sync(tm.mask, ba, own, G), b = __shfl_sync(tm.mask, bbv, own, G);
-    const float dx = __shfl_sync(tm.mask, bdx, own, G), dy = __shfl_sync(tm.mask, bdy, own, G);
+    const Q dx = __shfl_sync(tm.mask, bdx, own, G), dy = __shfl_sync(tm.mask, bdy, own, G);
     p.b = __shfl_sync(tm.mask, bbound, own, G);
     p.k = kb;
     p.ia = a;
     if (b >= 0) {
         p.ib = b;
-        p.ax = -2.f * dx;
-        p.ay = -2.f * dy;
+        p.ax = (Q)-2 * dx;
+        p.ay = (Q)-2 * dy;
     } else {
         const int s = -1 - b;
         p.ib = -1;
-        p.ax = (s == 0) ? 1.f : (s == 1) ? -1.f : 0.f;
-        p.ay = (s == 2) ? 1.f : (s == 3) ? -1.f : 0.f;
+        p.ax = (s == 0) ? (Q)1 : (s == 1) ? (Q)-1 : (Q)0;
+        p.ay = (s == 2) ? (Q)1 : (s == 3) ? (Q)-1 : (Q)0;
     }
     return true;
 }
 
 // Mark row key k active / inactive in the lane that holds it.
-template <int NMAX>
-__device__ __forceinline__ void lane_rows_mark(LaneRows<NMAX>& R, int k, bool on) {
+template <int NMAX, typename Q>
+__device__ __forceinline__ void lane_rows_mark(LaneRows<NMAX, Q>& R, int k, bool on) {
 #pragma unroll
-    for (int d = 0; d < LaneRows<NMAX>::PR; ++d)
+    for (int d = 0; d < LaneRows<NMAX, Q>::PR; ++d)
         if (R.key[d] == k) R.on = on ? (R.on | (1u << d)) : (R.on & ~(1u << d));
 #pragma unroll
     for (int s = 0; s < 4; ++s)
         if (R.bkey[s] == k) {
-            const unsigned bit = 1u << (LaneRows<NMAX>::PR + s);
+            const unsigned bit = 1u << (LaneRows<NMAX, Q>::PR + s);
             R.on = on ? (R.on | bit) : (R.on & ~bit);
         }
 }
 
-template <int G, int NMAX>
-__device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, const QPConsts<float>& c,
-                                 QPWork<float, NMAX>& Wscan) {
-    constexpr int RPL = (NMAX + G - 1) / G;
-    constexpr int AS = InvWork<NMAX>::A;
-    if (tm.lane == 0) W.free_slots = (AS >= 64) ? ~0ull : ((1ull << AS) - 1ull);
+// Order-preserving map of a float to an unsigned key (for redux.sync minima).
+__device__ __forceinline__ unsigned float_order_key(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Every lane of the team gets the minimum of v over the team and the team lane that holds it
+// (the lowest such lane).
+template <int G>
+__device__ __forceinline__ int team_min_lane(const Team<G>& tm, float v) {
+    const unsigned k = float_order_key(v);
+    const unsigned m = __reduce_min_sync(tm.mask, k);
+    return (__ffs(__ballot_sync(tm.mask, k == m)) - 1) & (G - 1);
+}
+
+// The work of one iteration is spread so that no lane walks the active set serially: the team
+// maxima and minima are redux.sync reductions; z, a robot's share of a_p - N r, comes from that
+// robot's own incident active rows (a bit mask per robot); the rank-one updates of M and B run
+// one active slot per lane over the variables.
+// Q: binary32 (the step's solver) or binary64 (the re-solve of a flagged QP); UW holds the
+// points and u (px, py, ux, uy per robot).  A QP whose active set outgrows the AS slots ends
+// with status 2.
+template <typename Q, int G, int NMAX, int AS, class UW>
+__device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int N,
+                                 const QPConsts<Q>& c, UW& Wscan) {
+    static_assert(G >= NMAX, "qp_solve_inv holds one robot per lane");
+    const int i = tm.lane;  // the lane's robot
+    if (i == 0) W.free_slots = (AS >= 64) ? ~0ull : ((1ull << AS) - 1ull);
+    if (i < NMAX) W.inc[i] = 0ull;
     tm.sync();
     QPResult res;
     res.status = 0;
@@ -793,84 +839,77 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, con
     res.iters = 0;
     res.flag = false;
     int q = 0;
-    static_assert(G >= NMAX, "qp_solve_inv holds one robot per lane");
-    LaneRows<NMAX> LR;
-    lane_rows_init<NMAX>(LR, tm.lane, N, Wscan.px, Wscan.py, c);
+    LaneRows<NMAX, Q> LR;
+    lane_rows_init<NMAX, Q>(LR, i, N, Wscan.px, Wscan.py, c);
     for (;;) {
-        float vbest;
-        RowInfo<float> p;
-        if (!scan_cached<G, NMAX>(tm, LR, tm.lane, Wscan.ux, Wscan.uy, c, p, vbest)) break;
+        Q vbest;
+        RowInfo<Q> p;
+        if (!scan_cached<Q, G, NMAX>(tm, LR, i, Wscan.ux, Wscan.uy, c, p, vbest)) break;
         if (++res.iters > c.max_iter || q >= AS) { res.status = 2; break; }
-        const float app = (p.ib >= 0 ? 2.f : 1.f) * (p.ax * p.ax + p.ay * p.ay);
+        const Q app = (p.ib >= 0 ? (Q)2 : (Q)1) * (p.ax * p.ax + p.ay * p.ay);
         // non-zeros of a_p: (variable, value)
         const int v0 = 2 * p.ia, v1 = 2 * p.ia + 1;
         const int v2 = p.ib >= 0 ? 2 * p.ib : v0, v3 = p.ib >= 0 ? 2 * p.ib + 1 : v1;
-        const float a0 = p.ax, a1 = p.ay, a2 = p.ib >= 0 ? -p.ax : 0.f, a3 = p.ib >= 0 ? -p.ay : 0.f;
-        float lam_p = 0.f;
+        const Q a0 = p.ax, a1 = p.ay, a2 = p.ib >= 0 ? -p.ax : (Q)0, a3 = p.ib >= 0 ? -p.ay : (Q)0;
+        Q lam_p = (Q)0;
         bool added = false;
         for (int guard = 0; guard <= AS + 1 && !added; ++guard) {
             // r = M^T a_p over the active slots, one slot per lane
-            for (int idx = tm.lane; idx < q; idx += G) {
+            for (int idx = i; idx < q; idx += G) {
                 const int t = W.act[idx];
                 W.r[t] = W.Mi[v0][t] * a0 + W.Mi[v1][t] * a1 + W.Mi[v2][t] * a2 + W.Mi[v3][t] * a3;
             }
             tm.sync();
-            // z = a_p - N r on the lane's own robots
-            float zx[RPL], zy[RPL];
-            float zzl = 0.f;
-#pragma unroll
-            for (int s = 0; s < RPL; ++s) {
-                const int i = tm.lane + s * G;
-                float ax = 0.f, ay = 0.f;
-                if (i < N) {
-                    if (p.ia == i) { ax += p.ax; ay += p.ay; }
-                    if (p.ib == i) { ax -= p.ax; ay -= p.ay; }
-                    for (int idx = 0; idx < q; ++idx) {
-                        const int t = W.act[idx];
-                        const float rt = W.r[t];
-                        if (W.sia[t] == i) { ax -= rt * W.sax[t]; ay -= rt * W.say[t]; }
-                        if (W.sib[t] == i) { ax += rt * W.sax[t]; ay += rt * W.say[t]; }
-                    }
+            // z = a_p - N r on the lane's robot: a_t is (sax, say) at robot sia, minus that at sib
+            Q zx = (Q)0, zy = (Q)0;
+            if (i < N) {
+                if (p.ia == i) { zx += p.ax; zy += p.ay; }
+                if (p.ib == i) { zx -= p.ax; zy -= p.ay; }
+                unsigned long long m = W.inc[i];
+                while (m) {
+                    const int t = __ffsll((long long)m) - 1;
+                    m &= m - 1ull;
+                    const Q rt = W.sia[t] == i ? -W.r[t] : W.r[t];
+                    zx += rt * W.sax[t];
+                    zy += rt * W.say[t];
                 }
-                zx[s] = ax;
-                zy[s] = ay;
-                zzl += ax * ax + ay * ay;
             }
-            const float zz = tm.sum(zzl);
-            float td = CUDART_INF_F;
+            const Q zz = tm.sum(zx * zx + zy * zy);
+            // the blocking multiplier: min over active slots with r > 0 of lam / r
+            Q td = qinf<Q>();
             int jb = 0x7fffffff;
-            for (int idx = tm.lane; idx < q; idx += G) {
+            for (int idx = i; idx < q; idx += G) {
                 const int t = W.act[idx];
-                const float rt = W.r[t];
-                if (rt > 0.f) {
-                    const float tj = W.lam[t] / rt;
+                const Q rt = W.r[t];
+                if (rt > (Q)0) {
+                    const Q tj = W.lam[t] / rt;
                     if (tj < td || (tj == td && idx < jb)) { td = tj; jb = idx; }
                 }
             }
-            tm.argmin(td, jb);
-            float apu;
+            if constexpr (std::is_same<Q, float>::value) {
+                const int own = team_min_lane(tm, td);
+                td = __shfl_sync(tm.mask, td, own, G);
+                jb = __shfl_sync(tm.mask, jb, own, G);
+            } else {
+                tm.argmin(td, jb);
+            }
+            Q apu;
             if (p.ib >= 0)
                 apu = p.ax * (Wscan.ux[p.ia] - Wscan.ux[p.ib]) + p.ay * (Wscan.uy[p.ia] - Wscan.uy[p.ib]);
             else
                 apu = p.ax * Wscan.ux[p.ia] + p.ay * Wscan.uy[p.ia];
-            const float sp = apu - p.b;
+            const Q sp = apu - p.b;
             const bool indep = zz > c.eps_dep * app;
             if (!indep) res.flag = true;
-            const float tf = indep ? sp / zz : CUDART_INF_F;
-            if (!(tf < CUDART_INF_F) && !(td < CUDART_INF_F)) { res.status = 1; break; }
-            const float st = tf < td ? tf : td;
+            const Q tf = indep ? sp / zz : qinf<Q>();
+            if (!(tf < qinf<Q>()) && !(td < qinf<Q>())) { res.status = 1; break; }
+            const Q st = tf < td ? tf : td;
             tm.sync();  // every lane is done reading u, r, lam
-            if (tf < CUDART_INF_F) {
-#pragma unroll
-                for (int s = 0; s < RPL; ++s) {
-                    const int i = tm.lane + s * G;
-                    if (i < N) {
-                        Wscan.ux[i] -= st * zx[s];
-                        Wscan.uy[i] -= st * zy[s];
-                    }
-                }
+            if (tf < qinf<Q>() && i < N) {
+                Wscan.ux[i] -= st * zx;
+                Wscan.uy[i] -= st * zy;
             }
-            for (int idx = tm.lane; idx < q; idx += G) {
+            for (int idx = i; idx < q; idx += G) {
                 const int t = W.act[idx];
                 W.lam[t] -= st * W.r[t];
             }
@@ -878,27 +917,26 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, con
             if (tf <= td) {
                 // add a_p in a free slot
                 const int sn = __ffsll((long long)W.free_slots) - 1;
-                const float inv = 1.f / zz;
-                // M <- [M - z r^T / zz, z / zz] on the lane's variables
-#pragma unroll
-                for (int s = 0; s < RPL; ++s) {
-                    const int i = tm.lane + s * G;
-                    if (i < N) {
-                        for (int ax = 0; ax < 2; ++ax) {
-                            const int v = 2 * i + ax;
-                            const float zv = ax == 0 ? zx[s] : zy[s];
-                            for (int idx = 0; idx < q; ++idx) {
-                                const int t = W.act[idx];
-                                W.Mi[v][t] -= zv * W.r[t] * inv;
-                            }
-                            W.Mi[v][sn] = zv * inv;
-                        }
-                    }
+                const Q inv = (Q)1 / zz;
+                if (i < N) {
+                    W.zx[i] = zx;
+                    W.zy[i] = zy;
+                    W.Mi[2 * i][sn] = zx * inv;      // the new column z / zz
+                    W.Mi[2 * i + 1][sn] = zy * inv;
                 }
-                // B <- [[B + r r^T / zz, -r / zz], [-r^T / zz, 1 / zz]]
-                for (int idx = tm.lane; idx < q; idx += G) {
+                tm.sync();
+                // M <- [M - z r^T / zz, z / zz] and B <- [[B + r r^T / zz, -r / zz], ...],
+                // one active slot per lane
+                for (int idx = i; idx < q; idx += G) {
                     const int t = W.act[idx];
-                    const float rt = W.r[t] * inv;
+                    const Q rt = W.r[t] * inv;
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k)
+                        if (k < N) {
+                            W.Mi[2 * k][t] -= W.zx[k] * rt;
+                            W.Mi[2 * k + 1][t] -= W.zy[k] * rt;
+                        }
+#pragma unroll 4
                     for (int jdx = 0; jdx < q; ++jdx) {
                         const int u = W.act[jdx];
                         W.Bi[t][u] += rt * W.r[u];
@@ -906,8 +944,9 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, con
                     W.Bi[t][sn] = -rt;
                     W.Bi[sn][t] = -rt;
                 }
+                if (i < N && (i == p.ia || i == p.ib)) W.inc[i] |= 1ull << sn;
                 tm.sync();
-                if (tm.lane == 0) {
+                if (i == 0) {
                     W.Bi[sn][sn] = inv;
                     W.sia[sn] = p.ia;
                     W.sib[sn] = p.ib;
@@ -919,48 +958,44 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, con
                     W.act[q] = sn;
                     W.free_slots &= ~(1ull << sn);
                 }
-                lane_rows_mark<NMAX>(LR, p.k, true);
+                lane_rows_mark<NMAX, Q>(LR, p.k, true);
                 ++q;
                 added = true;
             } else {
                 // drop the blocking row (list position jb, slot j)
                 const int j = W.act[jb];
                 tm.sync();
-                const float bjj = W.Bi[j][j];
-                const float ibjj = 1.f / bjj;
-                // M <- M_{:,-j} - M_{:,j} B_{j,-j} / B_jj
-#pragma unroll
-                for (int s = 0; s < RPL; ++s) {
-                    const int i = tm.lane + s * G;
-                    if (i < N) {
-                        for (int ax = 0; ax < 2; ++ax) {
-                            const int v = 2 * i + ax;
-                            const float mj = W.Mi[v][j] * ibjj;
-                            for (int idx = 0; idx < q; ++idx) {
-                                const int t = W.act[idx];
-                                if (t != j) W.Mi[v][t] -= mj * W.Bi[j][t];
-                            }
-                        }
-                    }
-                }
-                // B <- B_{-j,-j} - B_{-j,j} B_{j,-j} / B_jj (rows t != j; row j read only)
-                for (int idx = tm.lane; idx < q; idx += G) {
+                const Q bjj = W.Bi[j][j];
+                const Q ibjj = (Q)1 / bjj;
+                // M <- M_{:,-j} - M_{:,j} B_{j,-j} / B_jj and
+                // B <- B_{-j,-j} - B_{-j,j} B_{j,-j} / B_jj, one slot t != j per lane (column and
+                // row j are only read)
+                for (int idx = i; idx < q; idx += G) {
                     const int t = W.act[idx];
                     if (t == j) continue;
-                    const float btj = W.Bi[t][j] * ibjj;
+                    const Q bjt = W.Bi[j][t] * ibjj;
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k)
+                        if (k < N) {
+                            W.Mi[2 * k][t] -= W.Mi[2 * k][j] * bjt;
+                            W.Mi[2 * k + 1][t] -= W.Mi[2 * k + 1][j] * bjt;
+                        }
+                    const Q btj = W.Bi[t][j] * ibjj;
+#pragma unroll 4
                     for (int jdx = 0; jdx < q; ++jdx) {
                         const int u = W.act[jdx];
                         if (u != j) W.Bi[t][u] -= btj * W.Bi[j][u];
                     }
                 }
-                lane_rows_mark<NMAX>(LR, W.sk[j], false);
+                if (i < N && (i == W.sia[j] || i == W.sib[j])) W.inc[i] &= ~(1ull << j);
+                lane_rows_mark<NMAX, Q>(LR, W.sk[j], false);
                 tm.sync();
-                if (tm.lane == 0) {
+                if (i == 0) {
                     for (int idx = jb; idx < q - 1; ++idx) W.act[idx] = W.act[idx + 1];
                     W.free_slots |= 1ull << j;
                 }
                 --q;
-                if (!(bjj > 0.f)) res.status = 2;
+                if (!(bjj > (Q)0)) res.status = 2;
             }
             tm.sync();
             if (res.status != 0) break;
@@ -971,22 +1006,19 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX>& W, int N, con
     res.q = q;
     if (res.status == 0 && q > 0) {
         bool small_h = false;
-        for (int idx = tm.lane; idx < q; idx += G) {
+        for (int idx = i; idx < q; idx += G) {
             const int t = W.act[idx];
             if (W.sib[t] >= 0) {
-                const float dx = Wscan.px[W.sia[t]] - Wscan.px[W.sib[t]];
-                const float dy = Wscan.py[W.sia[t]] - Wscan.py[W.sib[t]];
+                const Q dx = Wscan.px[W.sia[t]] - Wscan.px[W.sib[t]];
+                const Q dy = Wscan.py[W.sia[t]] - Wscan.py[W.sib[t]];
                 if (dx * dx + dy * dy - c.r2 < c.h_flag) small_h = true;
             }
         }
         if (tm.any(small_h)) res.flag = true;
     }
-    if (res.status == 1) {
-#pragma unroll
-        for (int s = 0; s < RPL; ++s) {
-            const int i = tm.lane + s * G;
-            if (i < N) { Wscan.ux[i] = 0.f; Wscan.uy[i] = 0.f; }
-        }
+    if (res.status == 1 && i < N) {
+        Wscan.ux[i] = (Q)0;
+        Wscan.uy[i] = (Q)0;
     }
     if (res.status != 0) res.flag = true;
     tm.sync();
@@ -1345,7 +1377,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
         // ---- barrier-certificate QP (binary32: explicit-inverse form; binary64: Cholesky form)
         QPResult res;
         if constexpr (std::is_same<R, float>::value && (NMAX > 4))
-            res = qp_solve_inv<G, NMAX>(tm, S.qp.s.inv, N, qc, W);
+            res = qp_solve_inv<float, G, NMAX>(tm, S.qp.s.inv, N, qc, W);
         else
             res = qp_solve<R, G, NMAX>(tm, W, N, qc);
         int qflags = (res.q > 0 || res.status != 0) ? 1 : 0;
@@ -1360,22 +1392,60 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
             dc.ymin = (double)k.ymin; dc.ymax = (double)k.ymax; dc.h_flag = (double)k.h_flag;
             dc.max_iter = 8 * NMAX + 16;
             dc.tol_abs = 1e-12; dc.tol_rel = 1e-12; dc.eps_dep = 1e-12; dc.tol_lam = 1e-10;
+            double pxd[RPL], pyd[RPL];
 #pragma unroll
             for (int s = 0; s < RPL; ++s) {
-                const int i = tm.lane + s * G;
-                if (i < N) {
-                    double sd, cd;
-                    sincos((double)th[s], &sd, &cd);
-                    D.px[i] = (double)x[s] + (double)k.l * cd;
-                    D.py[i] = (double)y[s] + (double)k.l * sd;
-                    D.u0x[i] = (double)u0x[s];
-                    D.u0y[i] = (double)u0y[s];
-                    D.ux[i] = D.u0x[i];
-                    D.uy[i] = D.u0y[i];
-                }
+                double sd, cd;
+                sincos((double)th[s], &sd, &cd);
+                pxd[s] = (double)x[s] + (double)k.l * cd;
+                pyd[s] = (double)y[s] + (double)k.l * sd;
             }
-            tm.sync();
-            const QPResult r64 = qp_solve<double, G, NMAX>(tm, D, N, dc);
+            QPResult r64;
+            r64.status = 2;
+            const double* rux = D.ux;
+            const double* ruy = D.uy;
+            if constexpr (NMAX > 4 && NMAX <= 20 && G >= NMAX) {
+                // the explicit-inverse form (binary64 issue is slow: its rank-one updates spread
+                // over the lanes need far fewer instructions than the Cholesky form's
+                // triangular solves); an active set beyond its slots falls back below, and so
+                // does the 32-robot class (its binary64 lane rows would not fit in registers)
+                F64Inv<NMAX>& F = S.qp.di;
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        F.px[i] = pxd[s];
+                        F.py[i] = pyd[s];
+                        F.u0x[i] = F.ux[i] = (double)u0x[s];
+                        F.u0y[i] = F.uy[i] = (double)u0y[s];
+                    }
+                }
+                tm.sync();
+                r64 = qp_solve_inv<double, G, NMAX>(tm, F.inv, N, dc, F);
+                rux = F.ux;
+                ruy = F.uy;
+            }
+            if (r64.status == 2) {
+                tm.sync();
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                    const int i = tm.lane + s * G;
+                    if (i < N) {
+                        D.px[i] = pxd[s];
+                        D.py[i] = pyd[s];
+                        D.u0x[i] = (double)u0x[s];
+                        D.u0y[i] = (double)u0y[s];
+                        D.ux[i] = D.u0x[i];
+                        D.uy[i] = D.u0y[i];
+                    }
+                }
+                tm.sync();
+                const int it = r64.iters;
+                r64 = qp_solve<double, G, NMAX>(tm, D, N, dc);
+                r64.iters += it;
+                rux = D.ux;
+                ruy = D.uy;
+            }
             res.status = r64.status;
             res.q = r64.q;
             res.iters += r64.iters;
@@ -1385,7 +1455,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
             for (int s = 0; s < RPL; ++s) {
                 const int i = tm.lane + s * G;
                 usx[s] = usy[s] = (R)0;
-                if (i < N) { usx[s] = (R)D.ux[i]; usy[s] = (R)D.uy[i]; }
+                if (i < N) { usx[s] = (R)rux[i]; usy[s] = (R)ruy[i]; }
             }
         }
         if (!resolved) {

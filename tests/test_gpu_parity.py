@@ -176,6 +176,29 @@ def test_teacher_forced_binary32(rl, case):
     assert err["rew"] < 1e-5 and err["obs"] < 1e-5
 
 
+@pytest.mark.parametrize("case", ["nav8", "nav20_near", "forage_uneven"])
+def test_teacher_forced_large_binary64_resolve(rl, case):
+    """The binary64 re-solve of the classes over four robots (the explicit-inverse form in
+    binary64, with the Cholesky form behind it for active sets beyond its slots): h_flag = 10 m^2
+    flags every QP that keeps an active pair row, so most steps are re-solved; the minimisers
+    against the oracle's, stepped from the same states."""
+    seed = 91
+    if case == "nav8":
+        g, o = make_pair(0, 8, h_flag=10.0)
+        n, steps = [8] * 128, 20
+    elif case == "nav20_near":
+        g, o = make_pair(0, 20, near_frac=0.3, h_flag=10.0)
+        n, steps = [20] * 40, 20
+    else:
+        g, o = make_pair(1, 10, episode_len=30, h_flag=10.0)
+        n, steps = list(np.random.default_rng(8).integers(5, 11, 200)), 20
+    err, flagged = _teacher_forced(rl, g, o, n, seed, steps)
+    print(f"\n{case} (h_flag 10): max errors {err}  fp64-resolved QPs {flagged}")
+    assert flagged > 0
+    assert err["u_star"] < U_TOL
+    assert err["pose"] < POSE_STEP_TOL and err["rew"] < 1e-5 and err["obs"] < 1e-5
+
+
 def test_largen_near_contact_default_flag(rl):
     """The 20-robot configuration at full size (1024 envs, 30% with a near pair) under the
     default re-solve flag (no binary64 re-solve for small h alone): after 30 scripted steps
