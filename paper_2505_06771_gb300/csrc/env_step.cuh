@@ -677,9 +677,9 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
 template <int NMAX, typename Q = float>
 struct LaneRows {
     static constexpr int PR = NMAX / 2 > 0 ? NMAX / 2 : 1;
-    Q dx[PR], dy[PR], bp[PR];
+    Q dx[PR], dy[PR], bp[PR], thr[PR];  // dx, dy: p_i - p_j (the lane's robot first)
     int j[PR], key[PR];
-    Q bb[4];
+    Q bb[4], bthr[4];
     int bkey[4];
     int np;
     unsigned on;  // bit d: pair row d active; bit PR + s: arena row s active
@@ -698,13 +698,13 @@ __device__ __forceinline__ void lane_rows_init(LaneRows<NMAX, Q>& R, int i, int 
         while (j >= N) j -= N;
         if (d >= R.np) j = i;
         const int a = min(i, j), b = max(i, j);
-        const Q sg = (a == i) ? (Q)1 : (Q)-1;
         R.j[d] = j;
         R.key[d] = (d < R.np) ? pair_index(a, b, N) * 32 + (i & 31) : 0x7fffffff;
-        R.dx[d] = sg * (px[i < N ? i : 0] - px[j < N ? j : 0]);
-        R.dy[d] = sg * (py[i < N ? i : 0] - py[j < N ? j : 0]);
+        R.dx[d] = px[i < N ? i : 0] - px[j < N ? j : 0];
+        R.dy[d] = py[i < N ? i : 0] - py[j < N ? j : 0];
         const Q h = R.dx[d] * R.dx[d] + R.dy[d] * R.dy[d] - c.r2;
         R.bp[d] = c.gamma * h * h * h;
+        R.thr[d] = c.tol_abs + c.tol_rel * fabs(R.bp[d]);
     }
     const Q pxi = px[i < N ? i : 0], pyi = py[i < N ? i : 0];
     const Q bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
@@ -713,6 +713,8 @@ __device__ __forceinline__ void lane_rows_init(LaneRows<NMAX, Q>& R, int i, int 
     R.bb[1] = c.kg * bx1 * bx1 * bx1;
     R.bb[2] = c.kg * by0 * by0 * by0;
     R.bb[3] = c.kg * by1 * by1 * by1;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) R.bthr[s] = c.tol_abs + c.tol_rel * fabs(R.bb[s]);
 #pragma unroll
     for (int s = 0; s < 4; ++s) R.bkey[s] = (i < N) ? (P + 4 * i + s) * 32 + (i & 31) : 0x7fffffff;
 }
@@ -723,27 +725,20 @@ template <typename Q, int G, int NMAX>
 __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NMAX, Q>& R, int i,
                                             const Q* ux, const Q* uy, const QPConsts<Q>& c,
                                             RowInfo<Q>& p, Q& vbest) {
+    constexpr int PR = LaneRows<NMAX, Q>::PR;
     Q vb = (Q)0;
-    int kb = 0x7fffffff, ba = -1, bbv = -1;
-    Q bdx = (Q)0, bdy = (Q)0, bbound = (Q)0;
+    int kb = 0x7fffffff, db = -1;  // the lane's most violated row: pair row d, or PR + arena side
     if (R.np > 0 || (R.bkey[0] != 0x7fffffff)) {
         const Q uxi = ux[i], uyi = uy[i];
 #pragma unroll
-        for (int d = 0; d < LaneRows<NMAX, Q>::PR; ++d) {
+        for (int d = 0; d < PR; ++d) {
             if (d < R.np && !((R.on >> d) & 1u)) {
                 const int j = R.j[d];
-                const Q sg = (i < j) ? (Q)1 : (Q)-1;
-                const Q dux = sg * (uxi - ux[j]), duy = sg * (uyi - uy[j]);
-                const Q v = (Q)-2 * (R.dx[d] * dux + R.dy[d] * duy) - R.bp[d];
-                if (v > c.tol_abs + c.tol_rel * fabs(R.bp[d]) &&
-                    (v > vb || (v == vb && R.key[d] < kb))) {
+                const Q v = (Q)-2 * (R.dx[d] * (uxi - ux[j]) + R.dy[d] * (uyi - uy[j])) - R.bp[d];
+                if (v > R.thr[d] && (v > vb || (v == vb && R.key[d] < kb))) {
                     vb = v;
                     kb = R.key[d];
-                    ba = min(i, j);
-                    bbv = max(i, j);
-                    bdx = R.dx[d];
-                    bdy = R.dy[d];
-                    bbound = R.bp[d];
+                    db = d;
                 }
             }
         }
@@ -751,17 +746,34 @@ __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NM
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const Q v = aus[s] - R.bb[s];
-            if (R.bkey[s] != 0x7fffffff && !((R.on >> (LaneRows<NMAX, Q>::PR + s)) & 1u) &&
-                v > c.tol_abs + c.tol_rel * fabs(R.bb[s]) &&
+            if (R.bkey[s] != 0x7fffffff && !((R.on >> (PR + s)) & 1u) && v > R.bthr[s] &&
                 (v > vb || (v == vb && R.bkey[s] < kb))) {
                 vb = v;
                 kb = R.bkey[s];
-                ba = i;
-                bbv = -1 - s;  // arena row s
-                bbound = R.bb[s];
+                db = PR + s;
             }
         }
     }
+    // the chosen row's descriptor: robots a < b, p_a - p_b and bound (arena side s: b = -1 - s)
+    int ba = i, bbv = -1;
+    Q bdx = (Q)0, bdy = (Q)0, bbound = (Q)0;
+#pragma unroll
+    for (int d = 0; d < PR; ++d)
+        if (d == db) {
+            const int j = R.j[d];
+            const Q sg = (i < j) ? (Q)1 : (Q)-1;
+            ba = min(i, j);
+            bbv = max(i, j);
+            bdx = sg * R.dx[d];
+            bdy = sg * R.dy[d];
+            bbound = R.bp[d];
+        }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (db == PR + s) {
+            bbv = -1 - s;
+            bbound = R.bb[s];
+        }
     // the team's largest violation (non-negative floats order as their bits; a binary64 one is
     // compared rounded to binary32, which only orders the iterations), held by the lowest lane
     // that has it
@@ -924,22 +936,27 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
                     W.Mi[2 * i][sn] = zx * inv;      // the new column z / zz
                     W.Mi[2 * i + 1][sn] = zy * inv;
                 }
+                // the robots where z is non-zero (z and r are sparse: rows of other clusters
+                // of robots keep exact zeros in M, B and r, so skipping them changes nothing)
+                unsigned zm = __ballot_sync(tm.mask, i < N && (zx != (Q)0 || zy != (Q)0));
+                zm = (G == 32) ? zm : ((zm >> tm.base) & ((1u << G) - 1u));
                 tm.sync();
                 // M <- [M - z r^T / zz, z / zz] and B <- [[B + r r^T / zz, -r / zz], ...],
                 // one active slot per lane
                 for (int idx = i; idx < q; idx += G) {
                     const int t = W.act[idx];
                     const Q rt = W.r[t] * inv;
-#pragma unroll
-                    for (int k = 0; k < NMAX; ++k)
-                        if (k < N) {
+                    if (rt != (Q)0) {
+                        for (unsigned m = zm; m; m &= m - 1u) {
+                            const int k = __ffs(m) - 1;
                             W.Mi[2 * k][t] -= W.zx[k] * rt;
                             W.Mi[2 * k + 1][t] -= W.zy[k] * rt;
                         }
 #pragma unroll 4
-                    for (int jdx = 0; jdx < q; ++jdx) {
-                        const int u = W.act[jdx];
-                        W.Bi[t][u] += rt * W.r[u];
+                        for (int jdx = 0; jdx < q; ++jdx) {
+                            const int u = W.act[jdx];
+                            W.Bi[t][u] += rt * W.r[u];
+                        }
                     }
                     W.Bi[t][sn] = -rt;
                     W.Bi[sn][t] = -rt;
@@ -967,6 +984,10 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
                 tm.sync();
                 const Q bjj = W.Bi[j][j];
                 const Q ibjj = (Q)1 / bjj;
+                // the robots where column j of M is non-zero (as above: exact zeros elsewhere)
+                unsigned mm = __ballot_sync(tm.mask, i < N && (W.Mi[2 * i][j] != (Q)0 ||
+                                                               W.Mi[2 * i + 1][j] != (Q)0));
+                mm = (G == 32) ? mm : ((mm >> tm.base) & ((1u << G) - 1u));
                 // M <- M_{:,-j} - M_{:,j} B_{j,-j} / B_jj and
                 // B <- B_{-j,-j} - B_{-j,j} B_{j,-j} / B_jj, one slot t != j per lane (column and
                 // row j are only read)
@@ -974,17 +995,20 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
                     const int t = W.act[idx];
                     if (t == j) continue;
                     const Q bjt = W.Bi[j][t] * ibjj;
-#pragma unroll
-                    for (int k = 0; k < NMAX; ++k)
-                        if (k < N) {
+                    if (bjt != (Q)0) {
+                        for (unsigned m = mm; m; m &= m - 1u) {
+                            const int k = __ffs(m) - 1;
                             W.Mi[2 * k][t] -= W.Mi[2 * k][j] * bjt;
                             W.Mi[2 * k + 1][t] -= W.Mi[2 * k + 1][j] * bjt;
                         }
+                    }
                     const Q btj = W.Bi[t][j] * ibjj;
+                    if (btj != (Q)0) {
 #pragma unroll 4
-                    for (int jdx = 0; jdx < q; ++jdx) {
-                        const int u = W.act[jdx];
-                        if (u != j) W.Bi[t][u] -= btj * W.Bi[j][u];
+                        for (int jdx = 0; jdx < q; ++jdx) {
+                            const int u = W.act[jdx];
+                            if (u != j) W.Bi[t][u] -= btj * W.Bi[j][u];
+                        }
                     }
                 }
                 if (i < N && (i == W.sia[j] || i == W.sib[j])) W.inc[i] &= ~(1ull << j);
