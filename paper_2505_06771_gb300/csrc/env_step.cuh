@@ -830,16 +830,145 @@ __device__ __forceinline__ int team_min_lane(const Team<G>& tm, float v) {
     return (__ffs(__ballot_sync(tm.mask, k == m)) - 1) & (G - 1);
 }
 
+// Warm start of the dual active-set method from a given active set A (used by the binary64
+// re-solve of a flagged QP, started from the binary32 solve's final active set: each binary64
+// iteration is costly, and that set is the answer or close to it).  The method may start from
+// any active set of independent rows whose equality-constrained minimiser has nonnegative
+// multipliers (Goldfarb-Idnani 1983): here the rows of A at the current points (lane i holds row
+// i: robots wa < wb, or arena side wside of robot wa when wb < 0, and its key), their Gram matrix
+// G = N^T N inverted in place by Gauss-Jordan elimination (one row per lane; the pivots are the
+// |z|^2 the iteration tests for dependence), lam = G^-1 (N^T u0 - b), M = N G^-1,
+// u = u0 - N lam.  A dependent row or a negative multiplier rejects the start (returns 0: the
+// solve begins from the empty set, nothing of it kept); else the factors, multipliers, slots,
+// incidence masks and row marks are those the iteration would hold with A active, and it
+// returns |A|.
+template <typename Q, int G, int NMAX, int AS, class UW>
+__device__ int qp_warm_start(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int N,
+                             const QPConsts<Q>& c, UW& Wscan, LaneRows<NMAX, Q>& LR, int q0,
+                             int wa, int wb, int wside, int wkey) {
+    const int i = tm.lane;  // row i of A (i < q0) and robot i (i < N)
+    Q rax = (Q)0, ray = (Q)0, rbd = (Q)0;
+    if (i < q0) {
+        if (wb >= 0) {
+            const Q dx = Wscan.px[wa] - Wscan.px[wb], dy = Wscan.py[wa] - Wscan.py[wb];
+            const Q h = dx * dx + dy * dy - c.r2;
+            rax = (Q)-2 * dx;
+            ray = (Q)-2 * dy;
+            rbd = c.gamma * h * h * h;
+        } else {
+            const Q pxi = Wscan.px[wa], pyi = Wscan.py[wa];
+            rax = (wside == 0) ? (Q)1 : (wside == 1) ? (Q)-1 : (Q)0;
+            ray = (wside == 2) ? (Q)1 : (wside == 3) ? (Q)-1 : (Q)0;
+            const Q d = (wside == 0) ? c.xmax - c.half_r - pxi
+                      : (wside == 1) ? pxi - c.xmin - c.half_r
+                      : (wside == 2) ? c.ymax - c.half_r - pyi
+                                     : pyi - c.ymin - c.half_r;
+            rbd = c.kg * d * d * d;
+        }
+        W.sia[i] = wa;
+        W.sib[i] = wb;
+        W.sk[i] = wkey;
+        W.sax[i] = rax;
+        W.say[i] = ray;
+        W.sb[i] = rbd;
+        W.act[i] = i;
+    }
+    tm.sync();
+    // G (row i per lane): a_t = e_t at robot sia_t and -e_t at sib_t
+    if (i < q0) {
+        for (int u = 0; u < q0; ++u) {
+            const int ua = W.sia[u], ub = W.sib[u];
+            const int sg = (wa == ua ? 1 : 0) - (wa == ub ? 1 : 0) +
+                           (wb >= 0 ? ((wb == ub ? 1 : 0) - (wb == ua ? 1 : 0)) : 0);
+            W.Bi[i][u] = (Q)sg * (rax * W.sax[u] + ray * W.say[u]);
+        }
+        W.r[i] = W.Bi[i][i];  // |a_i|^2, the scale of the pivot test
+    }
+    tm.sync();
+    bool ok = true;
+    for (int kk = 0; kk < q0 && ok; ++kk) {
+        const Q pv = W.Bi[kk][kk];
+        ok = pv > c.eps_dep * W.r[kk];
+        const Q d = (Q)1 / pv;
+        tm.sync();
+        if (ok && i == kk) {
+            for (int j = 0; j < q0; ++j) W.Bi[kk][j] *= d;
+            W.Bi[kk][kk] = d;
+        }
+        tm.sync();
+        if (ok && i < q0 && i != kk) {
+            const Q f = W.Bi[i][kk];
+            W.Bi[i][kk] = (Q)0;
+            for (int j = 0; j < q0; ++j) W.Bi[i][j] -= f * W.Bi[kk][j];
+        }
+        tm.sync();
+    }
+    if (!ok) return 0;
+    // lam = G^-1 (N^T u0 - b): u still holds u0
+    if (i < q0) {
+        Q au = rax * Wscan.ux[wa] + ray * Wscan.uy[wa];
+        if (wb >= 0) au -= rax * Wscan.ux[wb] + ray * Wscan.uy[wb];
+        W.r[i] = au - rbd;
+    }
+    tm.sync();
+    Q lam = (Q)0;
+    if (i < q0)
+        for (int u = 0; u < q0; ++u) lam += W.Bi[i][u] * W.r[u];
+    if (__any_sync(tm.mask, i < q0 && lam < -c.tol_lam)) return 0;
+    lam = lam > (Q)0 ? lam : (Q)0;
+    // M = N G^-1 (column i per lane), the multipliers, the incidence masks
+    if (i < q0) {
+        for (int v = 0; v < 2 * N; ++v) W.Mi[v][i] = (Q)0;
+        for (int u = 0; u < q0; ++u) {
+            const Q w = W.Bi[u][i];
+            const int ua = W.sia[u], ub = W.sib[u];
+            const Q ex = w * W.sax[u], ey = w * W.say[u];
+            W.Mi[2 * ua][i] += ex;
+            W.Mi[2 * ua + 1][i] += ey;
+            if (ub >= 0) {
+                W.Mi[2 * ub][i] -= ex;
+                W.Mi[2 * ub + 1][i] -= ey;
+            }
+        }
+        W.lam[i] = lam;
+        atomicOr(&W.inc[wa], 1ull << i);
+        if (wb >= 0) atomicOr(&W.inc[wb], 1ull << i);
+    }
+    if (i == 0) W.free_slots &= ~((q0 >= 64) ? ~0ull : ((1ull << q0) - 1ull));
+    tm.sync();
+    // u = u0 - N lam on the lane's robot
+    if (i < N) {
+        Q ux = Wscan.ux[i], uy = Wscan.uy[i];
+        for (unsigned long long m = W.inc[i]; m; m &= m - 1ull) {
+            const int t = __ffsll((long long)m) - 1;
+            const Q lt = W.sia[t] == i ? W.lam[t] : -W.lam[t];
+            ux -= lt * W.sax[t];
+            uy -= lt * W.say[t];
+        }
+        Wscan.ux[i] = ux;
+        Wscan.uy[i] = uy;
+    }
+    // the rows of A marked active in the lanes that hold them (key: row index * 32 + lane)
+    for (int u = 0; u < q0; ++u) {
+        const int k = W.sk[u];
+        if ((k & 31) == (i & 31)) lane_rows_mark<NMAX, Q>(LR, k, true);
+    }
+    tm.sync();
+    return q0;
+}
+
 // The work of one iteration is spread so that no lane walks the active set serially: the team
 // maxima and minima are redux.sync reductions; z, a robot's share of a_p - N r, comes from that
 // robot's own incident active rows (a bit mask per robot); the rank-one updates of M and B run
 // one active slot per lane over the variables.
 // Q: binary32 (the step's solver) or binary64 (the re-solve of a flagged QP); UW holds the
 // points and u (px, py, ux, uy per robot).  A QP whose active set outgrows the AS slots ends
-// with status 2.
+// with status 2.  warm_q > 0 (binary64 only): start from the active set of warm_q rows that the
+// lanes hold (qp_warm_start) instead of the empty set.
 template <typename Q, int G, int NMAX, int AS, class UW>
 __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int N,
-                                 const QPConsts<Q>& c, UW& Wscan) {
+                                 const QPConsts<Q>& c, UW& Wscan, int warm_q = 0, int wa = 0,
+                                 int wb = -1, int wside = 0, int wkey = 0x7fffffff) {
     static_assert(G >= NMAX, "qp_solve_inv holds one robot per lane");
     const int i = tm.lane;  // the lane's robot
     if (i == 0) W.free_slots = (AS >= 64) ? ~0ull : ((1ull << AS) - 1ull);
@@ -853,6 +982,11 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
     int q = 0;
     LaneRows<NMAX, Q> LR;
     lane_rows_init<NMAX, Q>(LR, i, N, Wscan.px, Wscan.py, c);
+    if constexpr (!std::is_same<Q, float>::value) {
+        if (warm_q > 0 && warm_q <= G && warm_q <= AS)
+            q = qp_warm_start<Q, G, NMAX, AS, UW>(tm, W, N, c, Wscan, LR, warm_q, wa, wb, wside,
+                                                  wkey);
+    }
     for (;;) {
         Q vbest;
         RowInfo<Q> p;
@@ -1433,6 +1567,20 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                 // over the lanes need far fewer instructions than the Cholesky form's
                 // triangular solves); an active set beyond its slots falls back below, and so
                 // does the 32-robot class (its binary64 lane rows would not fit in registers)
+                // the binary32 solve's final active rows, the binary64 solve's start (read before
+                // the binary64 work overwrites them)
+                const int q32 = (res.status == 0) ? res.q : 0;
+                int wa = 0, wb = -1, wside = 0, wkey = 0x7fffffff;
+                if (tm.lane < q32) {
+                    const InvWork<NMAX>& W32 = S.qp.s.inv;
+                    const int t = W32.act[tm.lane];
+                    wa = W32.sia[t];
+                    wb = W32.sib[t];
+                    wkey = W32.sk[t];
+                    const float ax = W32.sax[t], ay = W32.say[t];
+                    wside = ax > 0.f ? 0 : ax < 0.f ? 1 : ay > 0.f ? 2 : 3;
+                }
+                tm.sync();
                 F64Inv<NMAX>& F = S.qp.di;
 #pragma unroll
                 for (int s = 0; s < RPL; ++s) {
@@ -1445,7 +1593,7 @@ __device__ void run_env(const LaunchArgs<R>& A, const Team<G>& tm, TeamSmem<R, N
                     }
                 }
                 tm.sync();
-                r64 = qp_solve_inv<double, G, NMAX>(tm, F.inv, N, dc, F);
+                r64 = qp_solve_inv<double, G, NMAX>(tm, F.inv, N, dc, F, q32, wa, wb, wside, wkey);
                 rux = F.ux;
                 ruy = F.uy;
             }
