@@ -11,7 +11,9 @@ host cores.
 
 Other workloads (--workload): tiny (16 x 4 x 100, binary64), uneven (8192 envs of 2..10 robots,
 Foraging, 500 steps, one persistent launch), largen (1024 x 20 x 300, 30% near pairs, binary32
-with binary64 re-solve), serving (Poisson arrivals, 60 GB budget, p50/p99 latency).
+with binary64 re-solve), serving (Poisson arrivals, 60 GB budget, p50/p99 latency), sweep
+(env-steps/s of the Navigation rollout over the number of environments, the GPU analogue of the
+paper's parallel-scaling experiment, Sec. 4.2 and Fig. 2).
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
 Under torchrun each rank runs its own batch (weak scaling, no data-path collective).
@@ -90,7 +92,8 @@ def _args():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="nav", choices=list(WORKLOADS) + ["serving", "policy"])
+    p.add_argument("--workload", default="nav",
+                   choices=list(WORKLOADS) + ["serving", "policy", "sweep"])
     p.add_argument("--hidden", type=int, default=128, help="policy: GRU width (App. A: 128-512)")
     p.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
@@ -307,8 +310,9 @@ def run_reference(a):
     if rank != 0:
         return
     import oracle
-    if a.workload == "serving":
-        print(json.dumps({"impl": "reference", "unavailable": "serving has no oracle leg"}))
+    if a.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference",
+                          "unavailable": f"the {a.workload} workload has no oracle leg"}))
         return
     w = WORKLOADS[a.workload]
     threads = os.cpu_count() or 1
@@ -742,6 +746,74 @@ def run_policy(a):
     env.close()
 
 
+SWEEP_ENVS = (1, 16, 128, 1024, 4096, 16384, 65536)
+
+
+def run_sweep(a):
+    """Navigation, 4 robots, 1000-step rollouts (10 episodes) at each number of environments
+    in SWEEP_ENVS, each launch shape picked by the autotuner: env-steps/s and ms per rollout
+    (mean of --steps rollouts after the warm-ups).  The paper measures the same scaling with
+    JAX on a CPU (Sec. 4.2, Fig. 2: 100K timesteps over a range of environment counts); its
+    values are in a figure only, so there is no number to compare with."""
+    import torch
+
+    import paper_2505_06771_gb300 as rl
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    rl.lib()
+    T = a.horizon if a.horizon > 0 else 1000
+    w = dict(WORKLOADS["nav"])
+    stream = torch.cuda.Stream()
+    rows_out = []
+    launches = 0
+    with Clocks(_gpu_index(local)) as clk:
+        for E in SWEEP_ENVS:
+            g = rl.config_default(0, precision=32, **_cfg_overrides(w))
+            with torch.cuda.stream(stream):
+                env = rl.Env(g, E, 4, seed=_rank_seed(0), stream=stream)
+                obs = torch.empty(T, E * 4, env.obs_dim, device="cuda")
+                rew = torch.empty(T, E, device="cuda")
+                done = torch.empty(T, E, dtype=torch.uint8, device="cuda")
+            stream.synchronize()
+            tuning = env.tune(min(T, 500)) if not a.no_tune else None
+            for _ in range(max(3, a.warmup)):
+                env.rollout(T, obs, rew, done)
+            stream.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(a.steps)]
+            for i in range(a.steps):
+                ev[i][0].record(stream)
+                env.rollout(T, obs, rew, done)
+                ev[i][1].record(stream)
+            stream.synchronize()
+            launches += a.steps
+            per = [s_.elapsed_time(e_) for s_, e_ in ev]
+            ms = statistics.mean(per)
+            rows_out.append({"n_envs": E, "ms_per_rollout": ms, "env_steps_per_s": E * T / (ms / 1e3),
+                             "robot_steps_per_s": 4 * E * T / (ms / 1e3),
+                             "p99_ms": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))],
+                             "tuning": tuning})
+            env.close()
+            del obs, rew, done
+            torch.cuda.empty_cache()
+    best = max(r["env_steps_per_s"] for r in rows_out)
+    line = {"metric": METRIC, "value": best, "unit": "env-steps/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": max(3, a.warmup), "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"navigation sweep over n_envs {list(SWEEP_ENVS)} x 4 robots x "
+                                   f"{T} steps, scripted nominal control, fp32",
+                       "l2": "trajectory outputs larger than L2 from 1024 envs on"},
+            "sweep": rows_out, "gpu_launches": launches, "clocks": clk.summary(),
+            "context": {"paper": "Sec. 4.2, Fig. 2: JAX on an Apple M4 Pro CPU, values in a "
+                                 "figure only (another machine: context, not a target)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -750,6 +822,8 @@ def main():
         run_serving(a)
     elif a.workload == "policy":
         run_policy(a)
+    elif a.workload == "sweep":
+        run_sweep(a)
     else:
         run_rollout(a)
 

@@ -310,7 +310,8 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
     const bool scripted = A.io.actions == nullptr;
     // the env's episode clock (the dynamics warp's, advanced by the published done flags)
     int t = live ? A.s.t[e] : 0, ep = live ? A.s.ep[e] : 0;
-    if (live) small_reset(tm, So, A, e, ep + 1, N);  // the launch's first episode end
+    // the launch's first episode end (read at step 2 or later: short launches skip it)
+    if (live && A.T > 2) small_reset(tm, So, A, e, ep + 1, N);
 
     for (int step = 0; step < A.T; ++step) {
         __syncwarp();
@@ -327,13 +328,13 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
         // the episode clock at the start of step + 1, then the noise of step + 3 and, after an
         // episode end, the next episode's initial state
         if (done) { t = 0; ++ep; } else { ++t; }
-        if (scripted) {
+        if (scripted && step + 3 < A.T) {
             int t3 = t + 1, ep3 = ep;
             if (t3 >= k.episode_len) { t3 = 0; ++ep3; }
             if (++t3 >= k.episode_len) { t3 = 0; ++ep3; }
             if (own) slot.noise[(step + 3) & 3][tiw][i] = split_noise(A.seed, e, ep3, i, t3);
         }
-        if (done) small_reset(tm, So, A, e, ep + 1, N);
+        if (done && step + 3 < A.T) small_reset(tm, So, A, e, ep + 1, N);
         // collisions and arena exits of the projected points after the Euler step (before any
         // reset), the team reward
         int col = 0, oob = 0;
