@@ -283,9 +283,11 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
         if (i == 0) {
             A.s.t[e] = t;
             A.s.ep[e] = ep;
-            int32_t* cn = A.s.counters + e * kNCount;  // collisions and arena: the output warp
-            cn[2] += c_succ; cn[3] += c_act; cn[4] += c_flag; cn[5] += c_inf;
-            cn[6] += c_ep; cn[7] += c_it;
+            // collisions and arena exits are the output warp's; reductions without a returned
+            // value, so that the warp does not wait for the old counts before it exits
+            int32_t* cn = A.s.counters + e * kNCount;
+            atomicAdd(cn + 2, c_succ); atomicAdd(cn + 3, c_act); atomicAdd(cn + 4, c_flag);
+            atomicAdd(cn + 5, c_inf); atomicAdd(cn + 6, c_ep); atomicAdd(cn + 7, c_it);
         }
     }
 }
@@ -400,8 +402,8 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
     if (live && i == 0) {
         if (A.io.ret) A.io.ret[e] = ret_acc;
         int32_t* cn = A.s.counters + e * kNCount;
-        cn[0] += c_col;
-        cn[1] += c_oob;
+        atomicAdd(cn, c_col);
+        atomicAdd(cn + 1, c_oob);
     }
 }
 

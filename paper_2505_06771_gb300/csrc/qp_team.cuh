@@ -166,12 +166,16 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
     int q = 0;
     Q vb;
     int r = pair_scan(R, U, act, vb);
-    if (r >= 0) {
-        // first row in closed form: u <- u - (v / |a|^2) a
+    {
+        // first row in closed form: u <- u - (v / |a|^2) a.  Every team runs it, a team with no
+        // violated row as a zero step on slot 0 that it does not keep (the teams of a warp then
+        // take no divergent branch here; measured faster on GB300 than a branch around it)
+        const bool has = r >= 0;
+        const int r0 = has ? r : 0;
         Q a[8], b, h;
-        team_row(R, r, a, b, h, c.r2);
+        team_row(R, r0, a, b, h, c.r2);
         const Q app = tdot(a, a);
-        const Q st = __fdividef(vb, app);
+        const Q st = has ? __fdividef(vb, app) : (Q)0;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             U[m] -= st * a[m];
@@ -180,12 +184,12 @@ __device__ __forceinline__ QPResult team_qp(const float (&Px)[4], const float (&
         lam[0] = st;
         dinv[0] = rsqrtf(app);
         L[0] = app * dinv[0];
-        hlow = (h < c.h_flag) ? 1u : 0u;
-        slots = (unsigned)r;
-        act = 1u << r;
-        q = 1;
-        res.iters = 1;
-        r = pair_scan(R, U, act, vb);
+        hlow = (has && h < c.h_flag) ? 1u : 0u;
+        slots = (unsigned)r0;
+        act = has ? (1u << r0) : 0u;
+        q = has ? 1 : 0;
+        res.iters = has ? 1 : 0;
+        r = pair_scan(R, U, act, vb);  // u is unchanged without a row: -1 again
     }
     bool all_rows = false;  // the arena rows are built and scanned
     for (;;) {
