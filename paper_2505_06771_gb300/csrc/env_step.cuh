@@ -677,12 +677,13 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
 template <int NMAX, typename Q = float>
 struct LaneRows {
     static constexpr int PR = NMAX / 2 > 0 ? NMAX / 2 : 1;
-    Q dx[PR], dy[PR], bp[PR], thr[PR];  // dx, dy: p_i - p_j (the lane's robot first)
+    // dx, dy: p_i - p_j (the lane's robot first); thr: the violation threshold, +inf for a row
+    // that is absent or in the active set (so that a scan skips it without a test)
+    Q dx[PR], dy[PR], bp[PR], thr[PR];
     int j[PR], key[PR];
     Q bb[4], bthr[4];
     int bkey[4];
     int np;
-    unsigned on;  // bit d: pair row d active; bit PR + s: arena row s active
 };
 
 template <int NMAX, typename Q>
@@ -690,7 +691,6 @@ __device__ __forceinline__ void lane_rows_init(LaneRows<NMAX, Q>& R, int i, int 
                                                const Q* py, const QPConsts<Q>& c) {
     const int nd = (N - 1) / 2;
     R.np = (i < N) ? nd + (((N & 1) == 0 && i < N / 2) ? 1 : 0) : 0;
-    R.on = 0u;
     const int P = N * (N - 1) / 2;
 #pragma unroll
     for (int d = 0; d < LaneRows<NMAX, Q>::PR; ++d) {
@@ -704,7 +704,7 @@ __device__ __forceinline__ void lane_rows_init(LaneRows<NMAX, Q>& R, int i, int 
         R.dy[d] = py[i < N ? i : 0] - py[j < N ? j : 0];
         const Q h = R.dx[d] * R.dx[d] + R.dy[d] * R.dy[d] - c.r2;
         R.bp[d] = c.gamma * h * h * h;
-        R.thr[d] = c.tol_abs + c.tol_rel * fabs(R.bp[d]);
+        R.thr[d] = (d < R.np) ? c.tol_abs + c.tol_rel * fabs(R.bp[d]) : qinf<Q>();
     }
     const Q pxi = px[i < N ? i : 0], pyi = py[i < N ? i : 0];
     const Q bx0 = c.xmax - c.half_r - pxi, bx1 = pxi - c.xmin - c.half_r;
@@ -714,7 +714,7 @@ __device__ __forceinline__ void lane_rows_init(LaneRows<NMAX, Q>& R, int i, int 
     R.bb[2] = c.kg * by0 * by0 * by0;
     R.bb[3] = c.kg * by1 * by1 * by1;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) R.bthr[s] = c.tol_abs + c.tol_rel * fabs(R.bb[s]);
+    for (int s = 0; s < 4; ++s) R.bthr[s] = (i < N) ? c.tol_abs + c.tol_rel * fabs(R.bb[s]) : qinf<Q>();
 #pragma unroll
     for (int s = 0; s < 4; ++s) R.bkey[s] = (i < N) ? (P + 4 * i + s) * 32 + (i & 31) : 0x7fffffff;
 }
@@ -726,42 +726,41 @@ __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NM
                                             const Q* ux, const Q* uy, const QPConsts<Q>& c,
                                             RowInfo<Q>& p, Q& vbest) {
     constexpr int PR = LaneRows<NMAX, Q>::PR;
+    // the lane's most violated row: pair row d, or PR + arena side (ties: the first in that
+    // order; only the order of the iterations depends on it)
     Q vb = (Q)0;
-    int kb = 0x7fffffff, db = -1;  // the lane's most violated row: pair row d, or PR + arena side
+    int db = -1;
     if (R.np > 0 || (R.bkey[0] != 0x7fffffff)) {
         const Q uxi = ux[i], uyi = uy[i];
 #pragma unroll
         for (int d = 0; d < PR; ++d) {
-            if (d < R.np && !((R.on >> d) & 1u)) {
-                const int j = R.j[d];
-                const Q v = (Q)-2 * (R.dx[d] * (uxi - ux[j]) + R.dy[d] * (uyi - uy[j])) - R.bp[d];
-                if (v > R.thr[d] && (v > vb || (v == vb && R.key[d] < kb))) {
-                    vb = v;
-                    kb = R.key[d];
-                    db = d;
-                }
+            const int j = R.j[d];
+            const Q v = (Q)-2 * (R.dx[d] * (uxi - ux[j]) + R.dy[d] * (uyi - uy[j])) - R.bp[d];
+            if (v > (R.thr[d] > vb ? R.thr[d] : vb)) {
+                vb = v;
+                db = d;
             }
         }
         const Q aus[4] = {uxi, -uxi, uyi, -uyi};
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const Q v = aus[s] - R.bb[s];
-            if (R.bkey[s] != 0x7fffffff && !((R.on >> (PR + s)) & 1u) && v > R.bthr[s] &&
-                (v > vb || (v == vb && R.bkey[s] < kb))) {
+            if (v > (R.bthr[s] > vb ? R.bthr[s] : vb)) {
                 vb = v;
-                kb = R.bkey[s];
                 db = PR + s;
             }
         }
     }
-    // the chosen row's descriptor: robots a < b, p_a - p_b and bound (arena side s: b = -1 - s)
-    int ba = i, bbv = -1;
+    // the chosen row's descriptor: key, robots a < b, p_a - p_b and bound (arena side s:
+    // b = -1 - s)
+    int kb = 0x7fffffff, ba = i, bbv = -1;
     Q bdx = (Q)0, bdy = (Q)0, bbound = (Q)0;
 #pragma unroll
     for (int d = 0; d < PR; ++d)
         if (d == db) {
             const int j = R.j[d];
             const Q sg = (i < j) ? (Q)1 : (Q)-1;
+            kb = R.key[d];
             ba = min(i, j);
             bbv = max(i, j);
             bdx = sg * R.dx[d];
@@ -771,6 +770,7 @@ __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NM
 #pragma unroll
     for (int s = 0; s < 4; ++s)
         if (db == PR + s) {
+            kb = R.bkey[s];
             bbv = -1 - s;
             bbound = R.bb[s];
         }
@@ -801,18 +801,17 @@ __device__ __forceinline__ bool scan_cached(const Team<G>& tm, const LaneRows<NM
     return true;
 }
 
-// Mark row key k active / inactive in the lane that holds it.
+// Mark row key k active (its threshold +inf: the scans skip it) or inactive (its threshold
+// back) in the lane that holds it.
 template <int NMAX, typename Q>
-__device__ __forceinline__ void lane_rows_mark(LaneRows<NMAX, Q>& R, int k, bool on) {
+__device__ __forceinline__ void lane_rows_mark(LaneRows<NMAX, Q>& R, int k, bool on,
+                                               const QPConsts<Q>& c) {
 #pragma unroll
     for (int d = 0; d < LaneRows<NMAX, Q>::PR; ++d)
-        if (R.key[d] == k) R.on = on ? (R.on | (1u << d)) : (R.on & ~(1u << d));
+        if (R.key[d] == k) R.thr[d] = on ? qinf<Q>() : c.tol_abs + c.tol_rel * fabs(R.bp[d]);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
-        if (R.bkey[s] == k) {
-            const unsigned bit = 1u << (LaneRows<NMAX, Q>::PR + s);
-            R.on = on ? (R.on | bit) : (R.on & ~bit);
-        }
+        if (R.bkey[s] == k) R.bthr[s] = on ? qinf<Q>() : c.tol_abs + c.tol_rel * fabs(R.bb[s]);
 }
 
 // Order-preserving map of a float to an unsigned key (for redux.sync minima).
@@ -951,7 +950,7 @@ __device__ int qp_warm_start(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int N,
     // the rows of A marked active in the lanes that hold them (key: row index * 32 + lane)
     for (int u = 0; u < q0; ++u) {
         const int k = W.sk[u];
-        if ((k & 31) == (i & 31)) lane_rows_mark<NMAX, Q>(LR, k, true);
+        if ((k & 31) == (i & 31)) lane_rows_mark<NMAX, Q>(LR, k, true, c);
     }
     tm.sync();
     return q0;
@@ -1109,7 +1108,7 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
                     W.act[q] = sn;
                     W.free_slots &= ~(1ull << sn);
                 }
-                lane_rows_mark<NMAX, Q>(LR, p.k, true);
+                lane_rows_mark<NMAX, Q>(LR, p.k, true, c);
                 ++q;
                 added = true;
             } else {
@@ -1146,7 +1145,7 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
                     }
                 }
                 if (i < N && (i == W.sia[j] || i == W.sib[j])) W.inc[i] &= ~(1ull << j);
-                lane_rows_mark<NMAX, Q>(LR, W.sk[j], false);
+                lane_rows_mark<NMAX, Q>(LR, W.sk[j], false, c);
                 tm.sync();
                 if (i == 0) {
                     for (int idx = jb; idx < q - 1; ++idx) W.act[idx] = W.act[idx + 1];
