@@ -814,6 +814,11 @@ __device__ __forceinline__ void lane_rows_mark(LaneRows<NMAX, Q>& R, int k, bool
         if (R.bkey[s] == k) R.bthr[s] = on ? qinf<Q>() : c.tol_abs + c.tol_rel * fabs(R.bb[s]);
 }
 
+// a / b for a step length: the hardware quotient in binary32 (about 2 ulp; a length only
+// scales a step), the correctly rounded one in binary64.
+__device__ __forceinline__ float step_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double step_div(double a, double b) { return a / b; }
+
 // Order-preserving map of a float to an unsigned key (for redux.sync minima).
 __device__ __forceinline__ unsigned float_order_key(float v) {
     const unsigned b = __float_as_uint(v);
@@ -1026,8 +1031,8 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
             for (int idx = i; idx < q; idx += G) {
                 const int t = W.act[idx];
                 const Q rt = W.r[t];
-                if (rt > (Q)0) {
-                    const Q tj = W.lam[t] / rt;
+                if (rt > (Q)1e-30) {  // a smaller positive r blocks only an unbounded step
+                    const Q tj = step_div(W.lam[t], rt);
                     if (tj < td || (tj == td && idx < jb)) { td = tj; jb = idx; }
                 }
             }
@@ -1046,7 +1051,7 @@ __device__ QPResult qp_solve_inv(const Team<G>& tm, InvWork<NMAX, Q, AS>& W, int
             const Q sp = apu - p.b;
             const bool indep = zz > c.eps_dep * app;
             if (!indep) res.flag = true;
-            const Q tf = indep ? sp / zz : qinf<Q>();
+            const Q tf = indep ? step_div(sp, zz) : qinf<Q>();
             if (!(tf < qinf<Q>()) && !(td < qinf<Q>())) { res.status = 1; break; }
             const Q st = tf < td ? tf : td;
             tm.sync();  // every lane is done reading u, r, lam
