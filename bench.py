@@ -153,17 +153,23 @@ def _source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(workload: str):
-    """dram bytes per launch recorded from an ncu capture of this exact kernel source."""
+def _ncu_traffic(workload: str, kernel: str = ""):
+    """dram bytes per launch recorded from an ncu capture of this exact kernel source: the line
+    for the kernel the rollout launched (traffic_bytes_per_launch[<kernel>]), else the
+    workload's single line."""
     path = os.path.join(ROOT, "profiles", f"ncu_rollout_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     hm = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not hm or hm.group(1) != _source_hash():
+    if not hm or hm.group(1) != _source_hash():
         return None
-    return float(m.group(1))
+    name = kernel.split(" ")[0]
+    for km in re.finditer(r"traffic_bytes_per_launch\[([^\]]+)\]:\s*([0-9.eE+]+)", txt):
+        if km.group(1) == name:
+            return float(km.group(2))
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
 
 
 def _peaks(key: str = "hbm_gbs", fallback: float = 6800.0):
@@ -525,7 +531,8 @@ def run_rollout(a):
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     peak, peak_src = _peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": _ncu_traffic(a.workload),
+            "frac": achieved / peak,
+            "traffic": _ncu_traffic(a.workload, _kernel_name(a.workload, tuning)),
             "peak_source": peak_src, "kernel": _kernel_name(a.workload, tuning),
             "algorithmic_bytes_per_launch": alg_bytes,
             "bytes_per_env_step": alg_bytes / (E * T)}
