@@ -15,9 +15,9 @@
 // costs the dynamics warp one barrier arrival and two shared stores per step.
 //
 // The output warp also takes two state-independent pieces of the step off the dynamics warp:
-//  * the action noise: after reading step s it draws the Philox words of step s + 3 into a
-//    ring of four steps that the dynamics warp reads (steps 0-2 of a launch are drawn by the
-//    dynamics warp itself);
+//  * the action noise: it draws the Philox words of a launch's first three steps before the
+//    dynamics warp starts (one extra handover arrival releases it), then after reading step s
+//    those of step s + 3, into a ring of four steps that the dynamics warp reads;
 //  * the auto-reset sample: after reading the step that began an episode (or before its first
 //    step, for the launch's first episode) it samples the next episode's initial poses, goals
 //    and levels into its own team record, which the dynamics warp reads at the episode's end.
@@ -93,6 +93,8 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
     __sincosf(th, &sn, &cs);
     int c_succ = 0, c_act = 0, c_flag = 0, c_inf = 0, c_ep = 0, c_it = 0;
     int last_reset = -1;  // the step of the last episode end (-1: none in this launch)
+    // the output warp has drawn the noise of the launch's first three steps
+    if (A.T > 0) split_wait(split_empty_id(p));
 
     for (int step = 0; step < A.T; ++step) {
         float npx = 0.f, npy = 0.f, dterm = 0.f;
@@ -110,9 +112,8 @@ static __device__ __forceinline__ void split_dynamics(const LaunchArgs<float>& A
                 ux = k.k_si * (gx - px);
                 uy = k.k_si * (gy - py);
                 cap_fast(ux, uy, k.vmax);
-                // the noise words: from the output warp's ring from step 3 on
-                const uint2 w = step >= 3 ? slot.noise[step & 3][tiw][i]
-                                          : split_noise(A.seed, e, ep, i, t);
+                // the noise words, drawn ahead by the output warp
+                const uint2 w = slot.noise[step & 3][tiw][i];
                 {
                     const float ex = __fmul_rn(__fsub_rn(unit24(w.x), 0.5f), k.noise_scale);
                     const float ey = __fmul_rn(__fsub_rn(unit24(w.y), 0.5f), k.noise_scale);
@@ -312,6 +313,16 @@ static __device__ __forceinline__ void split_outputs(const LaunchArgs<float>& A,
     const bool scripted = A.io.actions == nullptr;
     // the env's episode clock (the dynamics warp's, advanced by the published done flags)
     int t = live ? A.s.t[e] : 0, ep = live ? A.s.ep[e] : 0;
+    // the noise of the launch's first three steps, then one handover arrival that releases the
+    // dynamics warp (every later arrival follows the reading of a step's slot)
+    if (live && scripted) {
+        int ts = t, es = ep;
+        for (int s0 = 0; s0 < 3 && s0 < A.T; ++s0) {
+            if (own) slot.noise[s0][tiw][i] = split_noise(A.seed, e, es, i, ts);
+            if (++ts >= k.episode_len) { ts = 0; ++es; }
+        }
+    }
+    if (A.T > 0) split_arrive(split_empty_id(p));
     // the launch's first episode end (read at step 2 or later: short launches skip it)
     if (live && A.T > 2) small_reset(tm, So, A, e, ep + 1, N);
 
