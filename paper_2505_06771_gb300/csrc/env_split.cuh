@@ -18,14 +18,16 @@
 //  * the action noise: it draws the Philox words of a launch's first three steps before the
 //    dynamics warp starts (one extra handover arrival releases it), then after reading step s
 //    those of step s + 3, into a ring of four steps that the dynamics warp reads;
-//  * the auto-reset sample: after reading the step that began an episode (or before its first
-//    step, for the launch's first episode) it samples the next episode's initial poses, goals
-//    and levels into its own team record, which the dynamics warp reads at the episode's end.
-// Both are read at least three steps after they were written; the barriers of the two steps in
-// between order the accesses (the writer has passed them only after finishing the write, the
-// reader waits on them), and a slot is rewritten only after the reader has arrived past its
-// read.  An episode end closer than that (episodes shorter than three steps, or the first one
-// ending before step 2) is sampled by the dynamics warp as before.
+//  * the auto-reset sample: after reading the step that began an episode (or before reading the
+//    launch's first step, for its first episode) it samples the next episode's initial poses,
+//    goals and levels into its own team record, which the dynamics warp reads at the episode's
+//    end.
+// Apart from the first three steps' noise, which the extra arrival orders, both are read at least
+// three steps after they were written; the barriers of the two steps in between order the
+// accesses (the writer has passed them only after finishing the write, the reader waits on
+// them), and a slot is rewritten only after the reader has arrived past its read.  An episode
+// end closer than that (episodes shorter than three steps, or the first one ending before step
+// 2) is sampled by the dynamics warp itself.
 //
 // Both warps of a pair run the same T steps over the same envs, every lane of both warps
 // executing every barrier (teams without an env skip only the work), so every barrier completes.
