@@ -141,3 +141,46 @@ def test_qp_kkt_residuals_along_rollouts(N, near):
         active += tr["qp"][:, 1].sum()
     assert active > 0
     assert worst < 1e-10
+
+
+@pytest.mark.parametrize("arena", ["default", "crowded"])
+def test_pair_rows_first_reaches_the_same_minimiser(arena):
+    """The 4-robot team QP of the GPU kernels solves over the pair rows alone first and checks
+    the arena rows only at that point: a minimiser of the relaxation that meets every row is the
+    minimiser of the whole QP.  Checked with the oracle's own solver on the QPs met along a
+    4-robot rollout: wherever the pair rows' minimiser meets the arena rows it equals the full
+    minimiser.  In the default arena the pair rows alone decide nearly every QP with an active
+    row; a crowded arena (1.2 m x 1.0 m, weak arena gain, strong noise) also meets QPs whose
+    relaxation leaves an arena row violated, where the full solve must go on."""
+    kw = {} if arena == "default" else dict(xmin=-0.6, xmax=0.6, ymin=-0.5, ymax=0.5,
+                                            kappa=0.05, noise_amp=0.3, init_margin=0.15)
+    c = oracle.default_cfg(oracle.NAV, n_max=4, **kw)
+    E, N = 256, 4
+    s = oracle.reset(c, 21, [N] * E)
+    P = N * (N - 1) // 2
+    checked = active = needs_arena = 0
+    for t in range(40):
+        x, y, th = s.x.reshape(E, N), s.y.reshape(E, N), s.th.reshape(E, N)
+        px, py = x + c["l"] * np.cos(th), y + c["l"] * np.sin(th)
+        _, _, _, tr = oracle.step(c, 21, s, trace=True)
+        u0 = tr["u_nom"].reshape(E, 2 * N)
+        for e in range(0, E, 4):
+            A, b = oracle.cbf_rows(c, px[e], py[e])
+            u_full, _, st, q, _ = oracle.qp_project(A, b, u0[e])
+            if st != 0 or q == 0:
+                continue
+            active += 1
+            u_pair, _, st_p, _, _ = oracle.qp_project(A[:P], b[:P], u0[e])
+            assert st_p == 0
+            viol = A[P:] @ u_pair - b[P:]
+            if np.all(viol <= 1e-12 * (1 + np.abs(b[P:]))):
+                checked += 1
+                assert np.abs(u_pair - u_full).max() < 1e-12
+            else:
+                needs_arena += 1
+                assert np.all(A @ u_full - b <= 1e-10 * (1 + np.abs(b)))
+    assert checked > 100
+    if arena == "default":
+        assert needs_arena <= 0.05 * active
+    else:
+        assert needs_arena > 0
