@@ -145,11 +145,21 @@ def _dist():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def _code_only(text: str) -> str:
+    """C++ source without its comments and blank space (what the compiler sees of it); string
+    literals in the sources here hold no comment markers."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.strip() for ln in text.splitlines() if ln.strip())
+
+
 def _source_hash() -> str:
+    """Hash of the CUDA library's code (comments excluded): a profile's counters hold for the
+    kernels built from the source it names."""
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_06771_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -660,7 +660,8 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
 }
 
 // ------------------------------------------------------------------------------------------
-// The same dual active-set method in explicit-inverse form (binary32 teams of 8..32 lanes).
+// The same dual active-set method in explicit-inverse form (teams of 8..32 lanes: the binary32
+// solve, and the binary64 re-solve of the 8..20-robot classes).
 // With N the active rows (as columns) and G = N^T N, it keeps B = G^-1 and M = N B in shared
 // memory, indexed by slot.  Then r = G^-1 N^T a_p = M^T a_p needs only the (at most four)
 // non-zeros of a_p -- one lane per active row, no sequential triangular solve -- and the block-
@@ -671,9 +672,9 @@ __device__ QPResult qp_solve(const Team<G>& tm, QPWork<Q, NMAX>& W, int N, const
 // ------------------------------------------------------------------------------------------
 
 // The barrier rows one lane evaluates in qp_solve_inv (teams with one robot per lane): its
-// circulant pair rows (partner, p_a - p_b, bound, key) and its four arena rows, computed once per
-// QP; "on" marks the ones currently in the active set.  key = row index * 32 + lane, so that an
-// argmax over keys breaks ties by row index and names the lane holding the row.
+// circulant pair rows (partner, p_i - p_j, bound, key) and its four arena rows, computed once per
+// QP; a row in the active set (or absent) carries an infinite threshold.  key = row index * 32 +
+// lane: it names the row in the active set and the lane holding it.
 template <int NMAX, typename Q = float>
 struct LaneRows {
     static constexpr int PR = NMAX / 2 > 0 ? NMAX / 2 : 1;
