@@ -204,7 +204,8 @@ struct NoInvWork {};
 
 // Slots of the binary64 explicit-inverse re-solve: enough for the active sets met (a QP that
 // needs more falls back to the Cholesky form) while its workspace stays within the binary32
-// one, so that the union below does not grow.
+// one for 16 to 32 robots, so that the union below does not grow there (8 robots: about 1 KB
+// more per team).
 template <int NMAX>
 constexpr int f64_inv_slots() { return NMAX <= 8 ? 2 * NMAX : (NMAX <= 20 ? 24 : 32); }
 
