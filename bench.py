@@ -109,6 +109,14 @@ def _args():
     return p.parse_args()
 
 
+def _kernels_per_rollout(tuning) -> int:
+    """Kernels one rollout launches: one (a single size class, or an uneven batch in one
+    persistent launch), else one per size class (the per-class launch modes)."""
+    if tuning and tuning.get("class_launch") in (0, 2) and len(tuning.get("classes", [])) > 1:
+        return len(tuning["classes"])
+    return 1
+
+
 def _kernel_name(workload: str, tuning) -> str:
     """The kernel the rollout launches: the tuner's (or the fixed) 4-robot variant."""
     if workload == "waypoint_pose":
@@ -617,7 +625,7 @@ def run_rollout(a):
                 "latency_ms": {"p50": float(np.percentile(per, 50)),
                                "p99": float(np.percentile(per, 99))},
                 "roofline": roof, "roofline_fp32": roof_fp32, "e2e": e2e,
-                "gpu_launches": a.steps,
+                "gpu_launches": a.steps * _kernels_per_rollout(tuning),
                 "clocks": clk.summary(),
                 "qp": {"active_step_frac": float(counters[:, 3].sum()) / env_steps_counted,
                        "fp64_resolved_frac": float(counters[:, 4].sum()) / env_steps_counted,
@@ -757,7 +765,7 @@ def run_policy(a):
                          "kernel": "rl::ptc::policy_step_tc (the policy's products), flops "
                                    "over the whole rollout time (policy and environment kernels)",
                          "flops_per_rollout": flops},
-            "e2e": None, "gpu_launches": a.steps, "clocks": clk.summary()}
+            "e2e": None, "gpu_launches": 2 * T * a.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     pol.close()
     env.close()

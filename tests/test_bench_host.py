@@ -36,3 +36,14 @@ def test_ncu_traffic_per_kernel_and_source(tmp_path, monkeypatch):
     (prof / "ncu_rollout_nav.md").write_text(
         f"traffic_bytes_per_launch: 300\nsource_hash: {bench._source_hash()}\n")
     assert bench._ncu_traffic("nav", "rl::anything") == 300.0
+
+
+def test_kernels_per_rollout():
+    assert bench._kernels_per_rollout(None) == 1
+    one = dict(nmax=4, lanes=4, block_threads=128, warp_envs=0, variant=3)
+    assert bench._kernels_per_rollout({"fixed": one}) == 1
+    three = [dict(one, nmax=n) for n in (4, 8, 16)]
+    assert bench._kernels_per_rollout({"class_launch": 1, "classes": three}) == 1
+    assert bench._kernels_per_rollout({"class_launch": 0, "classes": three}) == 3
+    assert bench._kernels_per_rollout({"class_launch": 2, "classes": three}) == 3
+    assert bench._kernels_per_rollout({"class_launch": 0, "classes": three[:1]}) == 1
