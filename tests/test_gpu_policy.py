@@ -50,9 +50,10 @@ def test_observe_matches_the_step_observation(rl):
     env.close()
 
 
-# The full batch (4096 envs) runs the policy kernel on 128 tiles and the step on every SM, each
-# launched while the other's last blocks run (programmatic dependent launches).
-@pytest.mark.parametrize("H,N,ep_len,E", [(128, 4, 100, 96), (256, 3, 4, 96), (128, 4, 4, 4096)])
+# H = 512 streams A's chunks through the stage ring (beyond the resident size) over four unit
+# blocks; the full batch (4096 envs) runs the policy kernel on 128 tiles.
+@pytest.mark.parametrize("H,N,ep_len,E", [(128, 4, 100, 96), (256, 3, 4, 96), (512, 4, 4, 96),
+                                           (128, 4, 4, 4096)])
 def test_policy_rollout_matches_reference_and_env(rl, H, N, ep_len, E):
     T = 9
     g = rl.config_default(0, scripted=0, n_max=N, episode_len=ep_len)
