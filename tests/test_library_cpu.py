@@ -1,5 +1,7 @@
 """CPU checks of the CUDA library: it builds for sm_103a, loads, exports every function that
-include/rl.h declares, and its defaults agree with the oracle's constants.  No CUDA calls."""
+include/rl.h declares, its defaults agree with the oracle's constants, and its calls reject
+invalid configurations, robot counts and null handles with RL_ERR_ARG before any CUDA call.  No
+CUDA calls."""
 import ctypes
 
 import pytest
@@ -88,3 +90,64 @@ def test_boundary_calls_cite_the_paper():
         k = hdr.index(f"rl_status {name}(")
         comment = hdr[hdr.rindex("/*", 0, k):k]
         assert passage in comment or passage in hdr[:hdr.index("#ifndef")], (name, passage)
+
+
+# Configurations rl_create rejects with RL_ERR_ARG before any CUDA call (so they run without a
+# GPU): each override breaks one rule of the configuration check.
+BAD_CONFIGS = [
+    (0, dict(scenario=7)), (0, dict(precision=16)), (0, dict(episode_len=0)),
+    (0, dict(max_attempts=0)), (0, dict(l=0.0)), (0, dict(vmax=-0.2)), (0, dict(wmax=0.0)),
+    (0, dict(dt=0.0)), (0, dict(r=-0.1)), (0, dict(xmax=-2.0)), (0, dict(ymax=-2.0)),
+    (0, dict(n_max=33)), (0, dict(n_max=-1)), (0, dict(block_threads=48)),
+    (0, dict(block_threads=512)), (0, dict(lanes=-1)), (0, dict(warp_envs=-1)),
+    (0, dict(goal_eps=-0.1)), (0, dict(controller=5)),
+    (0, dict(controller=1, pose_k1=0.0)),
+    (1, dict(r_max=0)), (1, dict(r_max=17)), (1, dict(n_res_min=3, n_res_max=2)),
+    (1, dict(n_res_max=99)), (1, dict(goal_eps=0.1)), (1, dict(controller=1)),
+]
+
+
+def _create(rl, cfg, n_envs, n_robots_uniform=4, per_env=None):
+    h = ctypes.c_void_p()
+    arr = None
+    if per_env is not None:
+        import numpy as np
+        arr = np.ascontiguousarray(per_env, dtype=np.int32)
+    st = rl.lib().rl_create(ctypes.byref(rl._to_struct(cfg)), n_envs,
+                            None if arr is None else arr.ctypes.data, n_robots_uniform, 0,
+                            None, ctypes.byref(h))
+    return st, h.value
+
+
+@pytest.mark.parametrize("scen,override", BAD_CONFIGS)
+def test_create_rejects_each_invalid_configuration(rl, scen, override):
+    g = rl.config_default(scen)
+    g.update(override)
+    st, h = _create(rl, g, 4)
+    assert st == 1 and h is None, (override, st)
+
+
+@pytest.mark.parametrize("n_envs,uniform,per_env,n_max", [
+    (0, 4, None, 0),                 # no envs
+    (4, 0, None, 0),                 # no robots
+    (4, 33, None, 0),                # more robots than a team holds
+    (3, 0, [4, 0, 2], 0),            # one env without robots
+    (3, 0, [4, 33, 2], 0),           # one env over the limit
+    (3, 0, [4, 6, 2], 4),            # n_max below the largest env
+])
+def test_create_rejects_robot_counts(rl, n_envs, uniform, per_env, n_max):
+    g = rl.config_default(rl.NAVIGATION, n_max=n_max)
+    st, h = _create(rl, g, n_envs, uniform, per_env)
+    assert st == 1 and h is None
+
+
+def test_calls_on_a_null_handle_are_argument_errors(rl):
+    L = rl.lib()
+    assert L.rl_step(None, None, None, None, None) == 1
+    assert L.rl_rollout(None, 10, None, None, None) == 1
+    assert L.rl_rollout_plain(None, 10, None, None, None) == 1
+    assert L.rl_rollout_host(None, None, 10, None, None, None) == 1
+    assert L.rl_sync(None) == 1
+    assert L.rl_obs_dim(None) == 0 and L.rl_n_envs(None) == 0 and L.rl_total_robots(None) == 0
+    assert L.rl_last_error(None) == b"null handle"
+    L.rl_destroy(None)  # a no-op
