@@ -1,5 +1,6 @@
 """Host logic of the benchmark (CPU): the source hash that ties a profile's DRAM counters to the
-kernels they were taken on, and the per-kernel lookup of those counters."""
+kernels they were taken on, the per-kernel lookup of those counters, the launch count, the
+clock-sample summary, the peak lookup and the algorithmic binary32 flop count."""
 import bench
 
 
@@ -47,3 +48,39 @@ def test_kernels_per_rollout():
     assert bench._kernels_per_rollout({"class_launch": 0, "classes": three}) == 3
     assert bench._kernels_per_rollout({"class_launch": 2, "classes": three}) == 3
     assert bench._kernels_per_rollout({"class_launch": 0, "classes": three[:1]}) == 1
+
+
+def test_clock_summary_median_max_and_reasons():
+    c = bench.Clocks(0)
+    c.lines = ["2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, 1201.0, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",  # unreadable sample: skipped
+               "garbage"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    c.lines = ["1500, 2070, 700, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
+
+
+def test_peaks_measured_or_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._peaks("hbm_gbs", 6800.0) == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6780.4, "bf16_tflops": 1988}')
+    assert bench._peaks("hbm_gbs", 6800.0) == (6780.4, "measured")
+    assert bench._peaks("bf16_tflops_sustained", 1700.0) == (1700.0, "fallback")
+
+
+def test_fp32_flops_per_env_step():
+    # 4 robots: per robot 85 + 4 * 3, per pair 21 (6 pairs), per env 4 + 2 -> 520 flops per
+    # env-step without active-set iterations; an iteration rescans 6 pair and 16 arena rows: 124
+    flops, per = bench._fp32_flops({"scenario": 0}, [4] * 10, qp_iters=0.0, env_steps=10)
+    assert flops == 5200.0 and per == 520.0
+    flops, per = bench._fp32_flops({"scenario": 0}, [4] * 10, qp_iters=3.2, env_steps=10)
+    assert abs(per - (520.0 + 0.32 * 124.0)) < 1e-9
+    # 20 robots: 20 * (85 + 76) + 21 * 190 + 22 = 7232
+    assert bench._fp32_flops({"scenario": 0}, [20], 0.0, 1)[1] == 7232.0
+    assert bench._fp32_flops({"scenario": 1}, [4], 0.0, 1) == (None, None)
