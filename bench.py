@@ -233,60 +233,99 @@ def _fp32_peak():
 
 
 class Clocks:
-    """nvidia-smi samples (100 ms) during the timed region."""
+    """nvidia-smi samples (every 100 ms) around the timed region.  The sampler is streaming
+    before the region starts (its first line is awaited, at most 3 s), every line is stamped on
+    arrival, and the summary keeps the lines that arrived from the region's start to one
+    interval after its end (a line reports the interval before it).  A region shorter than the
+    interval may hold none: the first line after its start then stands for it, and
+    `in_region` says so.  If no line came before the region (a sampler that buffers its output,
+    or a slow start) the arrival times say nothing, and the summary takes every line
+    (`in_region` null)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    INTERVAL_S = 0.1
 
     def __init__(self, index: int):
         self.index = index
-        self.lines = []
+        self.lines = []  # (host time of arrival, line)
         self.proc = None
+        self.t0 = self.t1 = None
+        self.streaming = False
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(int(self.INTERVAL_S * 1000))],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            self._wait_for(lambda: self.lines, 3.0)
+            self.streaming = bool(self.lines)
         except (OSError, ValueError):
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
+
+    def _wait_for(self, cond, limit_s: float):
+        end = time.perf_counter() + limit_s
+        while not cond() and time.perf_counter() < end and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *exc):
+        self.t1 = time.perf_counter()
         if self.proc:
+            if self.streaming:
+                # the line that reports the region's last interval
+                self._wait_for(lambda: self.lines and self.lines[-1][0] > self.t1,
+                               2 * self.INTERVAL_S + 0.05)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    @staticmethod
+    def _parse(line: str):
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 7:
+            return None
+        try:
+            return float(parts[0]), float(parts[1]), parts[3:7]
+        except ValueError:
+            return None
+
     def summary(self):
-        sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[3:7]):
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        stamped = [(t, self._parse(ln)) for t, ln in self.lines]
+        stamped = [(t, v) for t, v in stamped if v is not None]
+        if not self.streaming and self.t0 is not None:
+            window, in_region = [v for _, v in stamped], None
+        else:
+            window = [v for t, v in stamped if t0 <= t <= t1 + self.INTERVAL_S]
+            in_region = True
+        if not window and in_region is not None:
+            after = [v for t, v in stamped if t >= t0]
+            window, in_region = after[:1], False
+        if not window:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "in_region": None if in_region is None else False}
+        reasons = set()
+        for _, _, flags in window:
+            for nm, v in zip(names, flags):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(v[0] for v in window),
+                "sm_max_mhz": max(v[1] for v in window), "reasons": sorted(reasons),
+                "samples": len(window), "in_region": in_region}
 
 
 def _robots(w):

@@ -52,18 +52,61 @@ def test_kernels_per_rollout():
 
 def test_clock_summary_median_max_and_reasons():
     c = bench.Clocks(0)
-    c.lines = ["2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
-               "1980, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
-               "2070, 2070, 1201.0, Not Active, Not Active, Not Active, Not Active",
-               "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",  # unreadable sample: skipped
-               "garbage"]
+    c.t0, c.t1, c.streaming = 10.0, 10.5, True
+    c.lines = [(9.9, "1200, 2070, 300.0, Not Active, Not Active, Not Active, Not Active"),  # before
+               (10.1, "2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active"),
+               (10.3, "1980, 2070, 1390.0, Not Active, Not Active, Not Active, Active"),
+               (10.55, "2070, 2070, 1201.0, Not Active, Not Active, Not Active, Not Active"),
+               (10.58, "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]"),  # unreadable
+               (10.59, "garbage"),
+               (10.9, "210, 2070, 100.0, Active, Not Active, Not Active, Not Active")]  # after
     s = c.summary()
     assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
-                 "samples": 3}
-    c.lines = ["1500, 2070, 700, Active, Not Active, Active, Not Active"]
+                 "samples": 3, "in_region": True}
+    c.lines = [(10.2, "1500, 2070, 700, Active, Not Active, Active, Not Active")]
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    # a region shorter than the sampling interval: the first line after its start stands for it
+    c.t0, c.t1 = 10.0, 10.01
+    c.lines = [(9.95, "1000, 2070, 1, Not Active, Not Active, Not Active, Not Active"),
+               (10.2, "2055, 2070, 1, Not Active, Not Active, Not Active, Not Active"),
+               (10.3, "900, 2070, 1, Not Active, Not Active, Not Active, Not Active")]
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["samples"] == 1 and s["in_region"] is False
     c.lines = []
     assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
+    # a sampler whose lines came only after the region (buffered output): every line counts
+    c.streaming = False
+    c.lines = [(11.0, "2070, 2070, 1, Not Active, Not Active, Not Active, Not Active"),
+               (11.0, "2040, 2070, 1, Not Active, Not Active, Not Active, Active")]
+    s = c.summary()
+    assert s["samples"] == 2 and s["in_region"] is None and s["sm_mhz"] == 2055.0
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_streams_through_the_region(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi that prints one sample every 20 ms after a start-up delay
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/usr/bin/env python3\n"
+                    "import sys, time\n"
+                    "time.sleep(0.2)\n"
+                    "while True:\n"
+                    "    print('2070, 2070, 800.0, Not Active, Not Active, Not Active, Not Active',"
+                    " flush=True)\n"
+                    "    time.sleep(0.02)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + ":" + __import__("os").environ["PATH"])
+    with bench.Clocks(0) as c:
+        assert c.lines, "the sampler streams before the region starts"
+        import time
+        time.sleep(0.3)
+    s = c.summary()
+    assert c.streaming and s["in_region"] and s["samples"] >= 5 and s["sm_mhz"] == 2070.0
+    assert c.proc.poll() is not None  # stopped
+    # no nvidia-smi at all: an empty summary, no wait
+    monkeypatch.setenv("PATH", str(tmp_path / "none"))
+    with bench.Clocks(0) as c:
+        pass
+    assert c.summary()["samples"] == 0
 
 
 def test_peaks_measured_or_fallback(tmp_path, monkeypatch):
